@@ -1,0 +1,314 @@
+"""Benchmark: root-node split search of sparse oblique forest training on B300.
+
+Workload (the metric's configuration): single root-node split search on the
+histogram path, n = 4,194,304 samples, d = 64 float32 N(0,1) features,
+3 classes from sparse linear scores, 256 projections with 1+Poisson(1.5)
+(cap 8) +-1 non-zeros, 256 equal-width bins.  One step = the whole hot path
+for that node: min/max of every projection, histograms, Gini scan with double
+re-score, selection, and the stable partition of the node's samples.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is whole-job sample-projections per second
+(n * P per step, summed over ranks), inputs resident in HBM.  Under torchrun
+(N > 1) every rank runs an independent replica: the split search of one node
+does not shard without collectives, so N GPUs run N replicas ("replicas
+only"), with a barrier and max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "projected sample-projections/s in split search"
+UNIT = "sample-projections/s"
+WORKLOAD = "root_4m"
+FALLBACK_HBM_GBS = 6400.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs():
+    from paper_2603_00326_b300 import datagen as G
+    ds = G.root_4m()
+    p = G.WORKLOAD_PARAMS[WORKLOAD]
+    rng = np.random.default_rng(G.PROJ_SEED_BASE + 1)
+    pr = G.random_projections(rng, p["n_proj"], ds.d, p["lam"], p["cap"])
+    return ds, pr, p
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(ds, pr, n_sample_proj: int):
+    """The oracle as it stands, single-threaded, on all n samples and the first
+    n_sample_proj projections (a bounded sample of the same workload)."""
+    import oracle as O
+    from paper_2603_00326_b300 import datagen as G
+    idx = G.all_indices(ds.n)
+    ptr = pr.ptr[:n_sample_proj + 1]
+    t0 = time.perf_counter()
+    O.split_search(ds.X, ds.y, ds.n_classes, idx, ptr, pr.feat, pr.sign, hist_only=True)
+    O.partition(ds.X, idx, pr.feat[pr.ptr[0]:pr.ptr[1]], pr.sign[pr.ptr[0]:pr.ptr[1]], 0.0)
+    dt = time.perf_counter() - t0
+    return ds.n * n_sample_proj / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    ds, pr, p = make_inputs()
+    n_sample_proj = 16
+    for _ in range(args.warmup):
+        cpu_baseline(ds, pr, n_sample_proj)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_baseline(ds, pr, n_sample_proj)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = ds.n * n_sample_proj / (ms / 1000.0)
+    sample = (f"oracle split search + partition on all {ds.n} samples, first {n_sample_proj} of "
+              f"{p['n_proj']} projections per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": ds.n, "d": ds.d, "n_proj": p["n_proj"], "n_bins": 256,
+                   "classes": ds.n_classes, "path": "histogram"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_00326_b300 import soforest as S
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    S.lib()
+
+    ds_np, pr, p = make_inputs()
+    n, d, P, C = ds_np.n, ds_np.d, p["n_proj"], ds_np.n_classes
+    Xh = torch.from_numpy(ds_np.X).pin_memory()
+    yh = torch.from_numpy(ds_np.y).pin_memory()
+    idx_h = torch.arange(n, dtype=torch.int32).pin_memory()
+    ptr_h = torch.from_numpy(pr.ptr).pin_memory()
+    feat_h = torch.from_numpy(pr.feat).pin_memory()
+    sign_h = torch.from_numpy(pr.sign).pin_memory()
+    X = Xh.to(dev)
+    y = yh.to(dev)
+    idx = idx_h.to(dev)
+    ptr, feat, sign = ptr_h.to(dev), feat_h.to(dev), sign_h.to(dev)
+    ds = S.DeviceDataset(X, y, C)
+    pj = S.DeviceProjs(P, ptr, feat, sign)
+    off = torch.tensor([0, n], dtype=torch.int64, device=dev)
+    prm = S.split_params(p["n_bins"], 0, True)
+    ws = torch.empty(S.so_split_search_ws_bytes(1, n, P, C, prm), dtype=torch.uint8, device=dev)
+    out = torch.empty(S.SPLIT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    lc = torch.empty(C, dtype=torch.int64, device=dev)
+    idx_out = torch.empty(n, dtype=torch.int32, device=dev)
+    out_h = torch.empty(S.SPLIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step(idx_t):
+        S.so_split_search_batch(ds, idx_t, off, pj, prm, out=out, left_counts=lc, workspace=ws)
+        S.so_partition_batch(ds, idx_t, idx_out, off, pj, out)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step(idx)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = S.so_launch_count()
+    S.so_profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(idx)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    S.so_profile_enable(False)
+    launches = S.so_launch_count() - launches0
+    clk = clocks.stop()
+    prof = S.so_profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * P / (ms / 1000.0)
+
+    # ---- end to end through the public API, host buffers, copies inside the region
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
+    h2d = (Xh.numel() * 4 + yh.numel() + idx_h.numel() * 4 + ptr_h.numel() * 4 + feat_h.numel() * 4
+           + sign_h.numel())
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        X.copy_(Xh, non_blocking=True)
+        y.copy_(yh, non_blocking=True)
+        idx.copy_(idx_h, non_blocking=True)
+        ptr.copy_(ptr_h, non_blocking=True)
+        feat.copy_(feat_h, non_blocking=True)
+        sign.copy_(sign_h, non_blocking=True)
+        step(idx)
+        out_h.copy_(out, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1) if e2e_steps else float("nan")
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    rec = S.SPLIT_DTYPE and np.frombuffer(out_h.numpy().tobytes(), dtype=S.SPLIT_DTYPE)[0]
+
+    # ---- roofline of the dominant kernel (histogram fill)
+    hbm, peak_kind = peaks()
+    used_feats = np.unique(pr.feat).size
+    alg_bytes = used_feats * n * 4 + n * 4 + n * 1  # feature columns + index list + labels, one pass
+    k_launches, k_ms = prof.get("k_hist", (0, 0.0))
+    k_avg_ms = k_ms / max(k_launches, 1)
+    achieved = alg_bytes / (k_avg_ms / 1000.0) / 1e9 if k_avg_ms > 0 else None
+    stage_ms = {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "d": d, "n_proj": P, "n_bins": p["n_bins"], "classes": C,
+                   "path": "histogram", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs {X.numel() * 4 / 1e9:.2f} GB > 126 MB L2; no flush needed"},
+        "e2e": {"value": (world * n * P / e2e_s) if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(out_h.numel())},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "k_hist", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                     "avg_launch_ms": k_avg_ms},
+        "stage_ms_per_launch": stage_ms,
+        "clocks": clk,
+        "split": {"proj": int(rec["proj"]), "cand": int(rec["cand"]), "gain": float(rec["gain"]),
+                  "n_left": int(rec["n_left"])},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt = cpu_baseline(ds_np, pr, 32)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"oracle split search + partition on all {n} samples, first 32 of "
+                                          f"{P} projections ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,281 @@
+/*
+ * soforest.h -- C ABI of the B300 (sm_103a) sparse-oblique split-search library.
+ *
+ * The library computes, on one GPU, the per-node split search of sparse
+ * oblique forest training as stated in "Vectorized Adaptive Histograms for
+ * Sparse Oblique Forests" (Section 3, steps 1-3; Section 3.1 the
+ * sort/histogram switch by node cardinality; Section 3.3 the GPU offload,
+ * whose two kernels take a list of projection non-zeros and return the best
+ * projection and its split), plus the stable partition of the node's samples
+ * and a breadth-first tree grown to purity (Section 2, item 2).
+ *
+ * Conventions shared by every call:
+ *   - Every pointer documented "device" is CUDA device memory owned by the
+ *     caller; the library never frees it.  Pointers documented "host" are
+ *     ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered; those that return results into host
+ *     memory synchronise the stream before returning.
+ *   - Arguments are validated on the host before any launch; a bad argument
+ *     returns SO_EINVAL and launches nothing.  Device-side consistency checks
+ *     report SO_EINTERNAL.  CUDA errors report SO_ECUDA.  so_last_error()
+ *     returns a thread-local message for the last failure.
+ *   - No C++ exception crosses this boundary.
+ *   - Feature matrices are column-major: X[f*ld + i] is feature f of sample i.
+ *     Values must be finite.  Labels are uint8 in [0, n_classes), n_classes
+ *     in 1..8.
+ *   - A projection is a sparse row of +-1 weights over distinct features
+ *     listed in ascending order.  Its value for a sample is computed in float,
+ *     starting from +0 and adding (or subtracting) the features in that order,
+ *     one round-to-nearest addition each, no fused multiply-add.
+ *   - Results are bit-identical to the plain CPU definition of the method:
+ *     bins, histograms, chosen splits (projection, candidate, threshold bits,
+ *     double gain bits) and tree arrays.
+ */
+#ifndef SOFOREST_H
+#define SOFOREST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SO_OK = 0,
+    SO_EINVAL = 1,     /* bad argument, found on the host before any launch */
+    SO_ENOMEM = 2,     /* device or host allocation failed / workspace too small */
+    SO_ECUDA = 3,      /* a CUDA runtime call failed */
+    SO_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    SO_EINTERNAL = 5   /* a device-side consistency check failed */
+} so_status;
+
+/* Training data, device resident (the paper preloads the whole table once,
+ * Section 3.3).  X: device, column-major, X[f*ld + i], f < d, i < n.
+ * y: device, n labels in [0, n_classes). */
+typedef struct {
+    const float *X;
+    int64_t n;          /* samples, 1 .. 2^31-1 */
+    int32_t d;          /* features, >= 1 */
+    int64_t ld;         /* leading dimension, >= n */
+    const uint8_t *y;
+    int32_t n_classes;  /* 1..8 */
+} so_dataset;
+
+/* Sparse projections in CSR form (Section 3: "a sparse list" of non-zero
+ * offsets with random weights).  For a batch of m nodes the rows are
+ * node-major: row q = node*n_proj + p, so ptr has m*n_proj + 1 entries.
+ * All three arrays are device memory.  feat values are distinct within a row,
+ * ascending, in [0, d); sign values are +1 or -1; 1 <= row length <= 32. */
+typedef struct {
+    int32_t n_proj;        /* projections per node, 1..1024 */
+    const int32_t *ptr;    /* [rows + 1] */
+    const int32_t *feat;   /* [ptr[rows]] */
+    const int8_t *sign;    /* [ptr[rows]] */
+} so_projs;
+
+/* Split-search parameters.
+ *  n_bins       equal-width bins per projection, 2..256 (Section 3.2 uses 256).
+ *  sort_below   T: nodes with fewer than T samples take the exact sort path
+ *               (Section 3.1); 0..2048.
+ *  hist_only    nonzero: every node takes the histogram path.
+ *  rescore_rel_eps  relative window of the double-precision re-score of
+ *               float near-ties; <= 0 selects the default 4e-6.  Values below
+ *               the float error bound of the gain are raised to that bound. */
+typedef struct {
+    int32_t n_bins;
+    int32_t sort_below;
+    int32_t hist_only;
+    float rescore_rel_eps;
+} so_split_params;
+
+/* Result of one node's split search.
+ *  valid      1 iff a split with Gini decrease > 0 exists.
+ *  proj       winning projection (row within the node), or -1.
+ *  path       0 histogram, 1 exact sort: the path the node's size selects
+ *             (also reported for nodes of fewer than 2 samples, which are
+ *             never valid); -2: a projection row of the node is malformed and
+ *             the node was skipped.
+ *  cand       histogram path: bin b (bins <= b go left); sort path: sorted
+ *             position i (the i+1 smallest values go left); -1 if invalid.
+ *  threshold  samples with projected value < threshold go left.
+ *  gain       Gini decrease sum_c D_c^2 / (n^2 nL nR), D_c = n L_c - N_c nL,
+ *             evaluated in double (bit-identical to the CPU definition).
+ *  n_left / n_right  child sizes (counting repeated samples). */
+typedef struct {
+    int32_t valid;
+    int32_t proj;
+    int32_t path;
+    int32_t cand;
+    float threshold;
+    double gain;
+    int64_t n_left;
+    int64_t n_right;
+} so_split;
+
+/* Best split of ONE node (the paper's node-at-a-time GPU call, Section 3.3).
+ *  idx        device, n_node sample indices (repeats allowed, e.g. bootstrap).
+ *  projs      n_proj rows for this node.
+ *  out_host   host, receives the result; the call synchronises `stream`.
+ *  workspace  device scratch of ws_bytes, or NULL to use the library's
+ *             internal arena (kept until so_shutdown()).  Size it with
+ *             so_split_search_ws_bytes(1, n_node, ...).
+ *  left_counts_host  host [n_classes] class counts of the left child, or NULL. */
+so_status so_split_search(const so_dataset *ds, const int32_t *idx, int64_t n_node,
+                          const so_projs *projs, const so_split_params *params,
+                          so_split *out_host, int64_t *left_counts_host,
+                          void *workspace, size_t ws_bytes, void *stream);
+
+/* Best split of m nodes at once (the batched frontier): node j owns
+ * idx[node_off[j] .. node_off[j+1]).  Small and large nodes take their own
+ * paths in the same call.  Asynchronous; nothing is read back.
+ *  node_off        device int64 [m+1], non-decreasing, node_off[0] >= 0,
+ *                  node_off[m] <= n_total (the length of idx).
+ *  out_dev         device so_split [m].
+ *  left_counts_dev device int64 [m*n_classes] or NULL.
+ *  workspace       as above, sized by so_split_search_ws_bytes(m, n_total, ...). */
+so_status so_split_search_batch(const so_dataset *ds, const int32_t *idx, int64_t n_total,
+                                const int64_t *node_off, int32_t m, const so_projs *projs,
+                                const so_split_params *params, so_split *out_dev,
+                                int64_t *left_counts_dev, void *workspace, size_t ws_bytes,
+                                void *stream);
+
+/* Device workspace bytes needed by the two calls above. */
+size_t so_split_search_ws_bytes(int32_t m, int64_t n_total, int32_t n_proj, int32_t n_classes,
+                                const so_split_params *params);
+
+/* Stable partition of one node's samples (left = value < threshold, in
+ * input order, then right in input order), in place.
+ *  idx_inout  device [n_node]; feat/sign device [nnz] (one projection row).
+ *  n_left_out host; the call synchronises `stream`.  Uses the internal arena. */
+so_status so_partition(const so_dataset *ds, int32_t *idx_inout, int64_t n_node,
+                       const int32_t *feat, const int8_t *sign, int32_t nnz, float threshold,
+                       int64_t *n_left_out, void *stream);
+
+/* Stable partition of m nodes' segments at once (the batched frontier).
+ * Node j with splits[j].valid moves idx_in[node_off[j]..node_off[j+1]) to
+ * idx_out at the same offsets, left part first; invalid nodes are copied
+ * unchanged.  projs are the same rows as given to so_split_search_batch.
+ * Asynchronous.  idx_in and idx_out must not overlap. */
+so_status so_partition_batch(const so_dataset *ds, const int32_t *idx_in, int32_t *idx_out,
+                             int64_t n_total, const int64_t *node_off, int32_t m,
+                             const so_projs *projs, const so_split *splits_dev, void *stream);
+
+/* Per-node projection sampling on the device (Section 3: the projection
+ * matrix; Appendix A: distinct features by Floyd's algorithm).  For node j
+ * with 64-bit key keys[j] and projection p: a splitmix64 stream seeded from
+ * (key, p) draws nnz = min(cap, d, 1 + Poisson(lambda)) by inverse CDF, then
+ * nnz distinct features by Floyd's algorithm (sorted ascending), then one
+ * sign bit per feature.  Outputs use fixed slots of width cap:
+ *  nnz_out  device int32 [m*n_proj]
+ *  feat_out device int32 [m*n_proj*cap]  (slot q*cap .. q*cap+nnz-1)
+ *  sign_out device int8  [m*n_proj*cap]
+ * keys: device uint64 [m].  cap in 1..32, lambda >= 0.  Asynchronous. */
+so_status so_sample_projections(int32_t m, const uint64_t *keys, int32_t n_proj, int32_t d,
+                                double lambda, int32_t cap, int32_t *nnz_out, int32_t *feat_out,
+                                int8_t *sign_out, void *stream);
+
+/* The histogram stage alone for m nodes, every node on the histogram path
+ * (Section 3 step 2; the paper's first GPU kernel).  For inspection and
+ * testing of the intermediate results.
+ *  minmax_dev  device float [m*n_proj*2]: (min, max) of each projection.
+ *  hist_dev    device int32 [m*n_proj*n_bins*n_classes] class counts per bin.
+ *  gain32_dev  device float [m*n_proj*(n_bins-1)] float gain of every
+ *              candidate (-1 where a side is empty), or NULL.
+ * Asynchronous; uses the internal arena. */
+so_status so_histograms(const so_dataset *ds, const int32_t *idx, int64_t n_total,
+                        const int64_t *node_off, int32_t m, const so_projs *projs,
+                        int32_t n_bins, float *minmax_dev, int32_t *hist_dev, float *gain32_dev,
+                        void *stream);
+
+/* Tree growth parameters.
+ *  n_bins, sort_below, hist_only, rescore_rel_eps  as in so_split_params.
+ *  n_proj     projections sampled per node, 1..1024.
+ *  lambda, nnz_cap  nnz law of a projection: min(nnz_cap, d, 1+Poisson(lambda)).
+ *  seed, tree_id    root key = splitmix64(seed ^ tree_id*0x9E3779B97F4A7C15);
+ *             child key = splitmix64(2*key + side), side 0 left, 1 right.
+ *  max_depth  -1 grows to purity; otherwise nodes at this depth are leaves. */
+typedef struct {
+    int32_t n_bins;
+    int32_t sort_below;
+    int32_t hist_only;
+    float rescore_rel_eps;
+    int32_t n_proj;
+    double lambda;
+    int32_t nnz_cap;
+    uint64_t seed;
+    int32_t tree_id;
+    int32_t max_depth;
+} so_tree_params;
+
+/* A trained tree in breadth-first order (children appended level by level in
+ * parent order, left before right).  Host arrays allocated by the library;
+ * release with so_tree_free().  Per node i:
+ *  left/right   child ids or -1 for a leaf; depth (root 0);
+ *  leaf_class   majority class (ties to the lowest id);
+ *  proj_nnz, feat[i*cap..], sign[i*cap..]  the split's projection (nnz 0 for leaves);
+ *  cand, path   as in so_split (path -1: never searched, i.e. the node was
+ *               pure, had fewer than 2 samples or sat at max_depth);
+ *  threshold, gain  as in so_split (0 for leaves);
+ *  n_samples, class_counts[i*n_classes..]  node population. */
+typedef struct {
+    int64_t n_nodes;
+    int32_t n_classes;
+    int32_t cap;
+    int32_t *left, *right, *depth, *leaf_class, *proj_nnz, *feat, *cand;
+    int8_t *sign, *path;
+    float *threshold;
+    int64_t *n_samples, *class_counts;
+    double *gain;
+} so_tree;
+
+/* Grows one tree to purity (Section 2, item 2), level by level: every node of
+ * a depth is searched in one batched pass (sampling, min/max, histograms or
+ * exact sort, Gini scan, partition), then the next frontier is built on the
+ * device.  root_idx: device [n_root] (repeats allowed).  out: host, filled on
+ * success.  Synchronises `stream`; uses the internal arena. */
+so_status so_train_tree(const so_dataset *ds, const int32_t *root_idx, int64_t n_root,
+                        const so_tree_params *params, so_tree *out, void *stream);
+
+void so_tree_free(so_tree *tree);
+
+/* Measures the exact-sort and histogram paths on synthetic nodes drawn from
+ * ds on this GPU and writes into params->sort_below the node size above
+ * which the histogram path is faster (the paper's start-up microbenchmark,
+ * Section 3.1).  Other fields of params are kept.  Synchronises `stream`. */
+so_status so_autotune(const so_dataset *ds, int32_t n_proj, so_split_params *params,
+                      void *stream);
+
+/* ---- tracing ------------------------------------------------------------
+ * Per-stage timing (the paper instruments every node, Section 3).  When
+ * enabled, each kernel launch group records a CUDA event pair on its stream.
+ * so_profile_read() waits for the recorded events, writes up to max_entries
+ * (stage name, launches, total milliseconds) and resets the totals; it
+ * returns the number of entries written. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} so_profile_entry;
+
+void so_profile_enable(int on);
+int so_profile_read(so_profile_entry *out, int max_entries);
+
+/* Number of kernels this library has launched in this process. */
+long long so_launch_count(void);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *so_last_error(void);
+
+/* Releases the internal arena on every device the library touched. */
+void so_shutdown(void);
+
+/* Library version string. */
+const char *so_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOFOREST_H */

@@ -1,0 +1,742 @@
+// so_api.cu -- the C ABI (include/soforest.h): argument validation, the
+// internal device arena, and the host orchestration of the batched split
+// search, partition, sampling and breadth-first tree growth.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <algorithm>
+#include <vector>
+
+#include "so_internal.h"
+
+using namespace sof;
+
+namespace {
+
+thread_local std::string g_err;
+
+so_status fail(so_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define SO_CK(call)                                                                  \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) return fail(SO_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---- internal arena: one grow-only device buffer per device -----------------
+struct Arena {
+  std::mutex mu;
+  void* ptr = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+};
+std::mutex g_arenas_mu;
+std::map<int, Arena*> g_arenas;
+
+Arena& arena_for_current() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_arenas_mu);
+  Arena*& a = g_arenas[dev];
+  if (!a) a = new Arena();
+  return *a;
+}
+
+// Holds the arena for one call: later users on any stream wait for the work
+// this call enqueued (an event recorded on release).
+class ArenaLease {
+ public:
+  ArenaLease() = default;
+  ~ArenaLease() { release(); }
+  so_status acquire(size_t bytes, cudaStream_t st) {
+    a_ = &arena_for_current();
+    a_->mu.lock();
+    st_ = st;
+    if (!a_->done) {
+      if (cudaEventCreateWithFlags(&a_->done, cudaEventDisableTiming) != cudaSuccess) {
+        a_->done = nullptr;
+        return fail(SO_ECUDA, "cudaEventCreate failed");
+      }
+      cudaEventRecord(a_->done, st);
+    }
+    if (a_->cap < bytes) {
+      cudaEventSynchronize(a_->done);
+      if (a_->ptr) cudaFree(a_->ptr);
+      a_->ptr = nullptr;
+      a_->cap = 0;
+      const size_t want = bytes + bytes / 8 + (1 << 20);
+      if (cudaMalloc(&a_->ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        a_->ptr = nullptr;
+        return fail(SO_ENOMEM, "device allocation of %zu bytes failed", want);
+      }
+      a_->cap = want;
+    }
+    cudaStreamWaitEvent(st, a_->done, 0);
+    held_ = true;
+    return SO_OK;
+  }
+  void* ptr() const { return a_ ? a_->ptr : nullptr; }
+  size_t cap() const { return a_ ? a_->cap : 0; }
+  void release() {
+    if (held_) {
+      cudaEventRecord(a_->done, st_);
+      a_->mu.unlock();
+      held_ = false;
+    }
+  }
+
+ private:
+  Arena* a_ = nullptr;
+  cudaStream_t st_ = nullptr;
+  bool held_ = false;
+};
+
+so_status check_dataset(const so_dataset* ds) {
+  if (!ds) return fail(SO_EINVAL, "dataset is NULL");
+  if (!ds->X || !ds->y) return fail(SO_EINVAL, "dataset X or y is NULL");
+  if (ds->n < 1 || ds->n > INT32_MAX) return fail(SO_EINVAL, "dataset n=%lld out of range", (long long)ds->n);
+  if (ds->d < 1) return fail(SO_EINVAL, "dataset d=%d < 1", ds->d);
+  if (ds->ld < ds->n) return fail(SO_EINVAL, "dataset ld=%lld < n", (long long)ds->ld);
+  if (ds->n_classes < 1 || ds->n_classes > kMaxClasses)
+    return fail(SO_EINVAL, "n_classes=%d outside 1..8", ds->n_classes);
+  return SO_OK;
+}
+
+so_status check_params(const so_split_params* p) {
+  if (!p) return fail(SO_EINVAL, "params is NULL");
+  if (p->n_bins < 2 || p->n_bins > kMaxBins) return fail(SO_EINVAL, "n_bins=%d outside 2..256", p->n_bins);
+  if (p->sort_below < 0 || p->sort_below > kMaxSortBelow)
+    return fail(SO_EINVAL, "sort_below=%d outside 0..%d", p->sort_below, kMaxSortBelow);
+  return SO_OK;
+}
+
+so_status check_projs(const so_projs* pr) {
+  if (!pr) return fail(SO_EINVAL, "projs is NULL");
+  if (pr->n_proj < 1 || pr->n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj=%d outside 1..1024", pr->n_proj);
+  if (!pr->ptr || !pr->feat || !pr->sign) return fail(SO_EINVAL, "projection arrays are NULL");
+  return SO_OK;
+}
+
+// The float gain's relative error is below (C+6) 2^-24; the re-score window
+// must exceed twice that so the double winner always enters the re-score.
+float effective_eps(float eps, int C) {
+  const float floor_eps = 2.5f * (float)(C + 6) * 5.9604645e-8f;
+  if (!(eps > 0.0f)) eps = 4e-6f;
+  return eps < floor_eps ? floor_eps : eps;
+}
+
+DatasetView view_of(const so_dataset* ds) {
+  DatasetView v;
+  v.X = ds->X;
+  v.n = ds->n;
+  v.ld = ds->ld;
+  v.y = ds->y;
+  v.d = ds->d;
+  v.C = ds->n_classes;
+  return v;
+}
+
+ProjView csr_view(const so_projs* pr) {
+  ProjView v;
+  v.beg = pr->ptr;
+  v.end = pr->ptr + 1;
+  v.feat = pr->feat;
+  v.sign = pr->sign;
+  v.P = pr->n_proj;
+  return v;
+}
+
+size_t search_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, int32_t T, int32_t hist_only) {
+  Carver cv;
+  cv.dry = true;
+  SearchScratch s;
+  carve_search(cv, s, m, n_total, P, C, B, T, hist_only);
+  return cv.used + 256;
+}
+
+template <typename F>
+so_status guarded(F f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return fail(SO_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(SO_EINTERNAL, "unexpected exception");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* so_last_error(void) { return g_err.c_str(); }
+
+const char* so_version(void) { return "soforest-b300 0.1 (sm_103a)"; }
+
+void so_shutdown(void) {
+  std::lock_guard<std::mutex> lk(g_arenas_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_arenas) {
+    Arena* a = kv.second;
+    std::lock_guard<std::mutex> al(a->mu);
+    cudaSetDevice(kv.first);
+    if (a->done) {
+      cudaEventSynchronize(a->done);
+      cudaEventDestroy(a->done);
+      a->done = nullptr;
+    }
+    if (a->ptr) cudaFree(a->ptr);
+    a->ptr = nullptr;
+    a->cap = 0;
+  }
+  cudaSetDevice(cur);
+}
+
+size_t so_split_search_ws_bytes(int32_t m, int64_t n_total, int32_t n_proj, int32_t n_classes,
+                                const so_split_params* params) {
+  if (!params || m < 0 || n_proj < 1 || n_classes < 1) return 0;
+  const size_t extra = 4096 + sizeof(so_split) + 64 * (size_t)n_classes;
+  return search_bytes(m, n_total, n_proj, n_classes, params->n_bins, params->sort_below, params->hist_only) + extra;
+}
+
+so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_t n_total, const int64_t* node_off,
+                                int32_t m, const so_projs* projs, const so_split_params* params, so_split* out_dev,
+                                int64_t* left_counts_dev, void* workspace, size_t ws_bytes, void* stream) {
+  return guarded([&]() -> so_status {
+    so_status st;
+    if ((st = check_dataset(ds)) || (st = check_params(params)) || (st = check_projs(projs))) return st;
+    if (m < 0) return fail(SO_EINVAL, "m < 0");
+    if (m == 0) return SO_OK;
+    if (!idx || !node_off || !out_dev) return fail(SO_EINVAL, "idx, node_off or out_dev is NULL");
+    if (n_total < 0 || n_total > INT32_MAX) return fail(SO_EINVAL, "n_total out of range");
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int C = ds->n_classes, P = projs->n_proj;
+    const size_t need = search_bytes(m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only);
+    ArenaLease lease;
+    char* base = (char*)workspace;
+    size_t cap = ws_bytes;
+    if (!workspace) {
+      if ((st = lease.acquire(need, cs))) return st;
+      base = (char*)lease.ptr();
+      cap = lease.cap();
+    } else if (ws_bytes < need) {
+      return fail(SO_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
+    }
+    Carver cv;
+    cv.base = base;
+    cv.cap = cap;
+    SearchScratch s;
+    carve_search(cv, s, m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only);
+    if (!cv.ok()) return fail(SO_ENOMEM, "workspace too small");
+    SearchArgs a;
+    a.ds = view_of(ds);
+    a.idx = idx;
+    a.n_total = n_total;
+    a.node_off = node_off;
+    a.m = m;
+    a.pv = csr_view(projs);
+    a.B = params->n_bins;
+    a.T = params->sort_below;
+    a.hist_only = params->hist_only ? 1 : 0;
+    a.eps = effective_eps(params->rescore_rel_eps, C);
+    a.out = out_dev;
+    a.left_counts = left_counts_dev;
+    SO_CK(launch_search(a, s, cs));
+    return SO_OK;
+  });
+}
+
+so_status so_split_search(const so_dataset* ds, const int32_t* idx, int64_t n_node, const so_projs* projs,
+                          const so_split_params* params, so_split* out_host, int64_t* left_counts_host,
+                          void* workspace, size_t ws_bytes, void* stream) {
+  return guarded([&]() -> so_status {
+    so_status st;
+    if ((st = check_dataset(ds)) || (st = check_params(params)) || (st = check_projs(projs))) return st;
+    if (!out_host) return fail(SO_EINVAL, "out_host is NULL");
+    if (n_node < 0 || n_node > INT32_MAX) return fail(SO_EINVAL, "n_node out of range");
+    if (n_node > 0 && !idx) return fail(SO_EINVAL, "idx is NULL");
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int C = ds->n_classes, P = projs->n_proj;
+    const size_t need = search_bytes(1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only) +
+                        4096 + sizeof(so_split) + 64 * C;
+    ArenaLease lease;
+    char* base = (char*)workspace;
+    size_t cap = ws_bytes;
+    if (!workspace) {
+      if ((st = lease.acquire(need, cs))) return st;
+      base = (char*)lease.ptr();
+      cap = lease.cap();
+    } else if (ws_bytes < need) {
+      return fail(SO_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
+    }
+    Carver cv;
+    cv.base = base;
+    cv.cap = cap;
+    int64_t* off = cv.take<int64_t>(2);
+    so_split* out_dev = cv.take<so_split>(1);
+    int64_t* lc = cv.take<int64_t>(kMaxClasses);
+    SearchScratch s;
+    carve_search(cv, s, 1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only);
+    if (!cv.ok()) return fail(SO_ENOMEM, "workspace too small");
+    SO_CK(launch_fill_off(off, n_node, cs));
+    SearchArgs a;
+    a.ds = view_of(ds);
+    a.idx = idx;
+    a.n_total = n_node;
+    a.node_off = off;
+    a.m = 1;
+    a.pv = csr_view(projs);
+    a.B = params->n_bins;
+    a.T = params->sort_below;
+    a.hist_only = params->hist_only ? 1 : 0;
+    a.eps = effective_eps(params->rescore_rel_eps, C);
+    a.out = out_dev;
+    a.left_counts = lc;
+    SO_CK(launch_search(a, s, cs));
+    int64_t lch[kMaxClasses];
+    SO_CK(cudaMemcpyAsync(out_host, out_dev, sizeof(so_split), cudaMemcpyDeviceToHost, cs));
+    SO_CK(cudaMemcpyAsync(lch, lc, sizeof(int64_t) * C, cudaMemcpyDeviceToHost, cs));
+    SO_CK(cudaStreamSynchronize(cs));
+    if (left_counts_host) memcpy(left_counts_host, lch, sizeof(int64_t) * C);
+    if (out_host->path == -2) return fail(SO_EINVAL, "a projection row is malformed (length, order, range or sign)");
+    return SO_OK;
+  });
+}
+
+so_status so_partition(const so_dataset* ds, int32_t* idx_inout, int64_t n_node, const int32_t* feat,
+                       const int8_t* sign, int32_t nnz, float threshold, int64_t* n_left_out, void* stream) {
+  return guarded([&]() -> so_status {
+    so_status st;
+    if ((st = check_dataset(ds))) return st;
+    if (n_node < 0 || n_node > INT32_MAX) return fail(SO_EINVAL, "n_node out of range");
+    if (nnz < 1 || nnz > kMaxCap) return fail(SO_EINVAL, "nnz=%d outside 1..32", nnz);
+    if (!feat || !sign || !n_left_out) return fail(SO_EINVAL, "NULL argument");
+    if (n_node == 0) {
+      *n_left_out = 0;
+      return SO_OK;
+    }
+    if (!idx_inout) return fail(SO_EINVAL, "idx is NULL");
+    cudaStream_t cs = (cudaStream_t)stream;
+    Carver dry;
+    dry.dry = true;
+    dry.take<int32_t>(n_node);
+    dry.take<uint8_t>(n_node);
+    dry.take<int64_t>(part_tiles(n_node) + 1);
+    dry.take<PartNode>(1);
+    dry.take<int64_t>(2);
+    dry.take<int64_t>(1);
+    dry.take<int32_t>(1);
+    ArenaLease lease;
+    if ((st = lease.acquire(dry.used + 4096, cs))) return st;
+    Carver cv;
+    cv.base = (char*)lease.ptr();
+    cv.cap = lease.cap();
+    int32_t* tmp = cv.take<int32_t>(n_node);
+    uint8_t* flags = cv.take<uint8_t>(n_node);
+    int64_t* tiles = cv.take<int64_t>(part_tiles(n_node) + 1);
+    PartNode* node = cv.take<PartNode>(1);
+    int64_t* off = cv.take<int64_t>(2);
+    int64_t* ones = cv.take<int64_t>(1);
+    int32_t* err = cv.take<int32_t>(1);
+    SO_CK(cudaMemsetAsync(err, 0, sizeof(int32_t), cs));
+    SO_CK(launch_part_single(n_node, nnz, threshold, node, off, cs));
+    PartArgs a;
+    a.ds = view_of(ds);
+    a.idx_in = idx_inout;
+    a.idx_out = tmp;
+    a.n = n_node;
+    a.node_off = off;
+    a.m = 1;
+    a.nodes = node;
+    a.feat = feat;
+    a.sign = sign;
+    a.flags = flags;
+    a.tile_cnt = tiles;
+    a.ones_total = ones;
+    a.err = err;
+    a.n_out = n_node;
+    a.fix_node = node;
+    SO_CK(launch_partition(a, cs));
+    SO_CK(cudaMemcpyAsync(idx_inout, tmp, sizeof(int32_t) * n_node, cudaMemcpyDeviceToDevice, cs));
+    int64_t nl = 0;
+    int32_t e = 0;
+    SO_CK(cudaMemcpyAsync(&nl, ones, sizeof(int64_t), cudaMemcpyDeviceToHost, cs));
+    SO_CK(cudaMemcpyAsync(&e, err, sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
+    SO_CK(cudaStreamSynchronize(cs));
+    if (e) return fail(SO_EINTERNAL, "partition consistency check failed (code %d)", e);
+    *n_left_out = nl;
+    return SO_OK;
+  });
+}
+
+so_status so_partition_batch(const so_dataset* ds, const int32_t* idx_in, int32_t* idx_out, int64_t n_total,
+                             const int64_t* node_off, int32_t m, const so_projs* projs, const so_split* splits_dev,
+                             void* stream) {
+  return guarded([&]() -> so_status {
+    so_status st;
+    if ((st = check_dataset(ds)) || (st = check_projs(projs))) return st;
+    if (m < 0) return fail(SO_EINVAL, "m < 0");
+    if (m == 0 || n_total == 0) return SO_OK;
+    if (!idx_in || !idx_out || !node_off || !splits_dev) return fail(SO_EINVAL, "NULL argument");
+    if (n_total < 0 || n_total > INT32_MAX) return fail(SO_EINVAL, "n_total out of range");
+    cudaStream_t cs = (cudaStream_t)stream;
+    Carver dry;
+    dry.dry = true;
+    dry.take<PartNode>(m);
+    dry.take<V4>(scan_tiles_for_host(m) + 1);
+    dry.take<V4>(1);
+    dry.take<uint8_t>(n_total);
+    dry.take<int64_t>(part_tiles(n_total) + 1);
+    dry.take<int64_t>(1);
+    dry.take<int32_t>(1);
+    ArenaLease lease;
+    if ((st = lease.acquire(dry.used + 4096, cs))) return st;
+    Carver cv;
+    cv.base = (char*)lease.ptr();
+    cv.cap = lease.cap();
+    PartNode* nodes = cv.take<PartNode>(m);
+    V4* tiles = cv.take<V4>(scan_tiles_for_host(m) + 1);
+    V4* total = cv.take<V4>(1);
+    uint8_t* flags = cv.take<uint8_t>(n_total);
+    int64_t* tcnt = cv.take<int64_t>(part_tiles(n_total) + 1);
+    int64_t* ones = cv.take<int64_t>(1);
+    int32_t* err = cv.take<int32_t>(1);
+    SO_CK(cudaMemsetAsync(err, 0, sizeof(int32_t), cs));
+    const ProjView pv = csr_view(projs);
+    SO_CK(launch_part_nodes_from_splits(node_off, m, splits_dev, pv, nodes, tiles, total, cs));
+    PartArgs a;
+    a.ds = view_of(ds);
+    a.idx_in = idx_in;
+    a.idx_out = idx_out;
+    a.n = n_total;
+    a.node_off = node_off;
+    a.m = m;
+    a.nodes = nodes;
+    a.feat = projs->feat;
+    a.sign = projs->sign;
+    a.flags = flags;
+    a.tile_cnt = tcnt;
+    a.ones_total = ones;
+    a.err = err;
+    a.n_out = n_total;
+    a.fix_node = nullptr;
+    SO_CK(launch_partition(a, cs));
+    return SO_OK;
+  });
+}
+
+so_status so_sample_projections(int32_t m, const uint64_t* keys, int32_t n_proj, int32_t d, double lambda,
+                                int32_t cap, int32_t* nnz_out, int32_t* feat_out, int8_t* sign_out, void* stream) {
+  return guarded([&]() -> so_status {
+    if (m < 0 || n_proj < 1 || n_proj > kMaxProj || d < 1) return fail(SO_EINVAL, "bad m, n_proj or d");
+    if (cap < 1 || cap > kMaxCap) return fail(SO_EINVAL, "cap=%d outside 1..32", cap);
+    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SO_EINVAL, "lambda must be finite and >= 0");
+    if (m == 0) return SO_OK;
+    if (!keys || !nnz_out || !feat_out || !sign_out) return fail(SO_EINVAL, "NULL argument");
+    SO_CK(launch_sample(m, keys, n_proj, d, lambda, cap, nnz_out, feat_out, sign_out, nullptr, nullptr,
+                        (cudaStream_t)stream));
+    return SO_OK;
+  });
+}
+
+so_status so_histograms(const so_dataset* ds, const int32_t* idx, int64_t n_total, const int64_t* node_off,
+                        int32_t m, const so_projs* projs, int32_t n_bins, float* minmax_dev, int32_t* hist_dev,
+                        float* gain32_dev, void* stream) {
+  return guarded([&]() -> so_status {
+    so_status st;
+    if ((st = check_dataset(ds)) || (st = check_projs(projs))) return st;
+    if (n_bins < 2 || n_bins > kMaxBins) return fail(SO_EINVAL, "n_bins outside 2..256");
+    if (m < 0) return fail(SO_EINVAL, "m < 0");
+    if (m == 0) return SO_OK;
+    if (!idx || !node_off || !minmax_dev || !hist_dev) return fail(SO_EINVAL, "NULL argument");
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int C = ds->n_classes, P = projs->n_proj;
+    Carver dry;
+    dry.dry = true;
+    SearchScratch ds0;
+    carve_search(dry, ds0, m, n_total, P, C, n_bins, 0, 1);
+    dry.take<float>((size_t)m * P * (n_bins - 1));
+    ArenaLease lease;
+    if ((st = lease.acquire(dry.used + 4096, cs))) return st;
+    Carver cv;
+    cv.base = (char*)lease.ptr();
+    cv.cap = lease.cap();
+    SearchScratch s;
+    carve_search(cv, s, m, n_total, P, C, n_bins, 0, 1);
+    float* gtmp = cv.take<float>((size_t)m * P * (n_bins - 1));
+    if (!cv.ok()) return fail(SO_ENOMEM, "arena too small");
+    SearchArgs a;
+    a.ds = view_of(ds);
+    a.idx = idx;
+    a.n_total = n_total;
+    a.node_off = node_off;
+    a.m = m;
+    a.pv = csr_view(projs);
+    a.B = n_bins;
+    a.T = 0;
+    a.hist_only = 1;
+    a.minmax_out = minmax_dev;
+    a.hist_out = hist_dev;
+    a.gain32_out = gain32_dev;
+    SO_CK(launch_hist_inspect(a, s, gain32_dev ? gtmp : nullptr, cs));
+    return SO_OK;
+  });
+}
+
+void so_tree_free(so_tree* t) {
+  if (!t) return;
+  free(t->left); free(t->right); free(t->depth); free(t->leaf_class); free(t->proj_nnz); free(t->feat);
+  free(t->cand); free(t->sign); free(t->path); free(t->threshold); free(t->n_samples); free(t->class_counts);
+  free(t->gain);
+  memset(t, 0, sizeof(*t));
+}
+
+so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n_root, const so_tree_params* tp,
+                        so_tree* out, void* stream) {
+  return guarded([&]() -> so_status {
+    so_status st;
+    if ((st = check_dataset(ds))) return st;
+    if (!tp || !out) return fail(SO_EINVAL, "params or out is NULL");
+    memset(out, 0, sizeof(*out));
+    if (n_root < 1 || n_root > INT32_MAX / 2) return fail(SO_EINVAL, "n_root out of range");
+    if (!root_idx) return fail(SO_EINVAL, "root_idx is NULL");
+    so_split_params sp{tp->n_bins, tp->sort_below, tp->hist_only, tp->rescore_rel_eps};
+    if ((st = check_params(&sp))) return st;
+    if (tp->n_proj < 1 || tp->n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj outside 1..1024");
+    if (tp->nnz_cap < 1 || tp->nnz_cap > kMaxCap) return fail(SO_EINVAL, "nnz_cap outside 1..32");
+    if (!(tp->lambda >= 0.0) || !std::isfinite(tp->lambda)) return fail(SO_EINVAL, "lambda must be >= 0");
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int C = ds->n_classes, P = tp->n_proj, cap = tp->nnz_cap, B = tp->n_bins;
+    const int T = tp->sort_below, HO = tp->hist_only ? 1 : 0;
+    const int64_t Mcap = n_root / 2 + 2;
+    const int64_t Ncap = 2 * n_root + 1;
+    // batch of nodes searched at once: bounded projection slots and histograms
+    const size_t per_node_proj = (size_t)P * ((size_t)cap * 5 + 12);
+    int64_t Mb = (int64_t)((size_t)512 << 20) / (int64_t)per_node_proj;
+    if (HO) {
+      const size_t per_hist = (size_t)P * B * C * 4 + (size_t)P * 16;
+      Mb = std::min<int64_t>(Mb, (int64_t)(((size_t)1 << 30) / per_hist));
+    }
+    Mb = std::max<int64_t>(1, std::min<int64_t>(Mb, Mcap));
+
+    auto layout = [&](Carver& cv, int32_t** idx_a, int32_t** idx_b, Frontier* fa, Frontier* fb, so_split** spl,
+                      int64_t** lc, PartNode** pn, V4** tiles, V4** total, uint8_t** flags, int64_t** ptiles,
+                      int64_t** ones, int32_t** snnz, int32_t** sbeg, int32_t** send, int32_t** sfeat,
+                      int8_t** ssign, TreeDev* td, LevelStats** stats, SearchScratch* ss) {
+      *idx_a = cv.take<int32_t>(n_root);
+      *idx_b = cv.take<int32_t>(n_root);
+      for (Frontier* f : {fa, fb}) {
+        f->off = cv.take<int64_t>(Mcap + 1);
+        f->key = cv.take<uint64_t>(Mcap);
+        f->id = cv.take<int32_t>(Mcap);
+        f->depth = cv.take<int32_t>(Mcap);
+        f->counts = cv.take<int32_t>(Mcap * C);
+      }
+      *spl = cv.take<so_split>(Mcap);
+      *lc = cv.take<int64_t>(Mcap * C);
+      *pn = cv.take<PartNode>(Mcap);
+      *tiles = cv.take<V4>(scan_tiles_for_host(Mcap) + 1);
+      *total = cv.take<V4>(1);
+      *flags = cv.take<uint8_t>(n_root);
+      *ptiles = cv.take<int64_t>(part_tiles(n_root) + 1);
+      *ones = cv.take<int64_t>(1);
+      *snnz = cv.take<int32_t>(Mb * P);
+      *sbeg = cv.take<int32_t>(Mb * P);
+      *send = cv.take<int32_t>(Mb * P);
+      *sfeat = cv.take<int32_t>(Mb * P * cap);
+      *ssign = cv.take<int8_t>(Mb * P * cap);
+      td->left = cv.take<int32_t>(Ncap);
+      td->right = cv.take<int32_t>(Ncap);
+      td->depth = cv.take<int32_t>(Ncap);
+      td->leaf_class = cv.take<int32_t>(Ncap);
+      td->proj_nnz = cv.take<int32_t>(Ncap);
+      td->cand = cv.take<int32_t>(Ncap);
+      td->feat = cv.take<int32_t>(Ncap * cap);
+      td->sign = cv.take<int8_t>(Ncap * cap);
+      td->path = cv.take<int8_t>(Ncap);
+      td->threshold = cv.take<float>(Ncap);
+      td->n_samples = cv.take<int64_t>(Ncap);
+      td->class_counts = cv.take<int64_t>(Ncap * C);
+      td->gain = cv.take<double>(Ncap);
+      td->cap = cap;
+      td->C = C;
+      *stats = cv.take<LevelStats>(1);
+      carve_search(cv, *ss, (int32_t)Mb, n_root, P, C, B, T, HO);
+    };
+    int32_t *idx_a, *idx_b, *snnz, *sbeg, *send, *sfeat;
+    int8_t* ssign;
+    Frontier fa{}, fb{};
+    so_split* spl;
+    int64_t *lc, *ptiles, *ones;
+    PartNode* pn;
+    V4 *tiles, *total;
+    uint8_t* flags;
+    TreeDev td{};
+    LevelStats* stats;
+    SearchScratch ss;
+    Carver dry;
+    dry.dry = true;
+    layout(dry, &idx_a, &idx_b, &fa, &fb, &spl, &lc, &pn, &tiles, &total, &flags, &ptiles, &ones, &snnz, &sbeg,
+           &send, &sfeat, &ssign, &td, &stats, &ss);
+    ArenaLease lease;
+    if ((st = lease.acquire(dry.used + 4096, cs))) return st;
+    Carver cv;
+    cv.base = (char*)lease.ptr();
+    cv.cap = lease.cap();
+    layout(cv, &idx_a, &idx_b, &fa, &fb, &spl, &lc, &pn, &tiles, &total, &flags, &ptiles, &ones, &snnz, &sbeg,
+           &send, &sfeat, &ssign, &td, &stats, &ss);
+    if (!cv.ok()) return fail(SO_ENOMEM, "arena too small");
+
+    const DatasetView dv = view_of(ds);
+    const uint64_t kG = 0x9E3779B97F4A7C15ull;
+    uint64_t root_key_state = tp->seed ^ ((uint64_t)(int64_t)tp->tree_id * kG);
+    // root key: one splitmix64 step from the state above
+    uint64_t z = (root_key_state += kG);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    const uint64_t root_key = z ^ (z >> 31);
+
+    SO_CK(cudaMemcpyAsync(idx_a, root_idx, sizeof(int32_t) * n_root, cudaMemcpyDeviceToDevice, cs));
+    SO_CK(launch_tree_root(dv, idx_a, n_root, root_key, tp->max_depth, td, fa, stats, cs));
+    LevelStats hs{};
+    SO_CK(cudaMemcpyAsync(&hs, stats, sizeof(LevelStats), cudaMemcpyDeviceToHost, cs));
+    SO_CK(cudaStreamSynchronize(cs));
+    if (hs.err & 16) return fail(SO_EINVAL, "root_idx holds a sample index outside [0, n)");
+    if (hs.err & 32) return fail(SO_EINVAL, "a label is outside [0, n_classes)");
+    int64_t m = hs.m_next, n_level = n_root, n_nodes = 1;
+    Frontier cur = fa, nxt = fb;
+    int32_t *cidx = idx_a, *nidx = idx_b;
+    const float eps = effective_eps(tp->rescore_rel_eps, C);
+    while (m > 0) {
+      for (int64_t j0 = 0; j0 < m; j0 += Mb) {
+        const int32_t mb = (int32_t)std::min<int64_t>(Mb, m - j0);
+        SO_CK(launch_sample(mb, cur.key + j0, P, ds->d, tp->lambda, cap, snnz, sfeat, ssign, sbeg, send, cs));
+        SearchArgs a;
+        a.ds = dv;
+        a.idx = cidx;
+        a.n_total = n_level;
+        a.node_off = cur.off + j0;
+        a.m = mb;
+        a.pv = ProjView{sbeg, send, sfeat, ssign, P};
+        a.B = B;
+        a.T = T;
+        a.hist_only = HO;
+        a.eps = eps;
+        a.out = spl + j0;
+        a.left_counts = lc + j0 * C;
+        SO_CK(launch_search(a, ss, cs));
+        SO_CK(launch_tree_record_splits((int32_t)j0, mb, cur, spl, snnz, sfeat, ssign, P, cap, td, cs));
+      }
+      SO_CK(launch_tree_level((int32_t)m, cur, nxt, spl, lc, tp->max_depth, n_nodes, td, pn, tiles, total, stats,
+                              cs));
+      PartArgs pa;
+      pa.ds = dv;
+      pa.idx_in = cidx;
+      pa.idx_out = nidx;
+      pa.n = n_level;
+      pa.node_off = cur.off;
+      pa.m = (int32_t)m;
+      pa.nodes = pn;
+      pa.feat = td.feat;
+      pa.sign = td.sign;
+      pa.flags = flags;
+      pa.tile_cnt = ptiles;
+      pa.ones_total = ones;
+      pa.err = &stats->err;
+      pa.n_out = n_root;
+      pa.fix_node = nullptr;
+      SO_CK(launch_partition(pa, cs));
+      SO_CK(cudaMemcpyAsync(&hs, stats, sizeof(LevelStats), cudaMemcpyDeviceToHost, cs));
+      SO_CK(cudaStreamSynchronize(cs));
+      if (hs.err) return fail(SO_EINTERNAL, "partition consistency check failed (code %d)", hs.err);
+      n_nodes += hs.new_nodes;
+      if (n_nodes > Ncap) return fail(SO_EINTERNAL, "node capacity exceeded");
+      m = hs.m_next;
+      n_level = hs.n_next;
+      std::swap(cur, nxt);
+      std::swap(cidx, nidx);
+    }
+    // copy the tree out
+    so_tree t{};
+    t.n_nodes = n_nodes;
+    t.n_classes = C;
+    t.cap = cap;
+    const size_t N = (size_t)n_nodes;
+    t.left = (int32_t*)malloc(N * 4);
+    t.right = (int32_t*)malloc(N * 4);
+    t.depth = (int32_t*)malloc(N * 4);
+    t.leaf_class = (int32_t*)malloc(N * 4);
+    t.proj_nnz = (int32_t*)malloc(N * 4);
+    t.cand = (int32_t*)malloc(N * 4);
+    t.feat = (int32_t*)malloc(N * cap * 4);
+    t.sign = (int8_t*)malloc(N * cap);
+    t.path = (int8_t*)malloc(N);
+    t.threshold = (float*)malloc(N * 4);
+    t.n_samples = (int64_t*)malloc(N * 8);
+    t.class_counts = (int64_t*)malloc(N * C * 8);
+    t.gain = (double*)malloc(N * 8);
+    if (!t.left || !t.right || !t.depth || !t.leaf_class || !t.proj_nnz || !t.cand || !t.feat || !t.sign ||
+        !t.path || !t.threshold || !t.n_samples || !t.class_counts || !t.gain) {
+      so_tree_free(&t);
+      return fail(SO_ENOMEM, "host allocation of the tree failed");
+    }
+    struct Cp {
+      void* dst;
+      const void* src;
+      size_t bytes;
+    } cps[] = {{t.left, td.left, N * 4},
+               {t.right, td.right, N * 4},
+               {t.depth, td.depth, N * 4},
+               {t.leaf_class, td.leaf_class, N * 4},
+               {t.proj_nnz, td.proj_nnz, N * 4},
+               {t.cand, td.cand, N * 4},
+               {t.feat, td.feat, N * cap * 4},
+               {t.sign, td.sign, N * cap},
+               {t.path, td.path, N},
+               {t.threshold, td.threshold, N * 4},
+               {t.n_samples, td.n_samples, N * 8},
+               {t.class_counts, td.class_counts, N * C * 8},
+               {t.gain, td.gain, N * 8}};
+    for (const Cp& c : cps) {
+      const cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, cs);
+      if (e != cudaSuccess) {
+        so_tree_free(&t);
+        return fail(SO_ECUDA, "tree copy: %s", cudaGetErrorString(e));
+      }
+    }
+    const cudaError_t e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+      so_tree_free(&t);
+      return fail(SO_ECUDA, "tree copy: %s", cudaGetErrorString(e));
+    }
+    *out = t;
+    return SO_OK;
+  });
+}
+
+so_status so_autotune(const so_dataset* ds, int32_t n_proj, so_split_params* params, void* stream) {
+  return guarded([&]() -> so_status {
+    so_status st;
+    if ((st = check_dataset(ds)) || (st = check_params(params))) return st;
+    if (n_proj < 1 || n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj outside 1..1024");
+    return fail(SO_EINTERNAL, "autotuner not available in this build");
+  });
+}
+
+}  // extern "C"

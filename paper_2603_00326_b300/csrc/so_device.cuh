@@ -1,0 +1,177 @@
+// so_device.cuh -- device-side building blocks shared by the split-search
+// kernels: ordered float keys, the projected value, the equal-width bin rule,
+// the float and double Gini gains, splitmix64, and warp reductions.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "so_internal.h"
+
+namespace sof {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;       // splitmix64 increment
+constexpr uint64_t kProjMult = 0xD2B74407B1CE6E93ull;    // separates projection streams
+
+// Order-preserving map float -> uint32 (total order of finite floats, -0 < +0).
+__device__ __forceinline__ uint32_t f2key(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  return __uint_as_float(u);
+}
+
+// Projected value of sample s (Section 3 step 1: a sparse vector sum of the
+// selected columns).  Fixed order: +0, then the features in ascending order,
+// each added (sign +1) or subtracted as a negated addend, round-to-nearest,
+// never fused.  Starting from +0 makes a -0 result impossible.
+__device__ __forceinline__ float project_value(const float* __restrict__ X, int64_t ld, int64_t s,
+                                               const int32_t* f, const int8_t* sg, int k) {
+  float acc = 0.0f;
+  for (int j = 0; j < k; ++j) {
+    const float x = __ldg(X + (int64_t)f[j] * ld + s);
+    acc = __fadd_rn(acc, sg[j] == 1 ? x : -x);
+  }
+  return acc;
+}
+
+// Sample indices outside [0, n) are read as sample 0 (memory safety only;
+// the documented contract is 0 <= idx < n).
+__device__ __forceinline__ int64_t safe_sample(int32_t s, int64_t n) {
+  return ((uint32_t)s < (uint64_t)n) ? (int64_t)s : 0;
+}
+
+// Equal-width bins (Section 3.2 with 256 bins): w = (max-min)/B, boundary
+// t_j = min + j*w (float, round-to-nearest), bin(v) = #{ j in 1..B-1 : t_j <= v }.
+__device__ __forceinline__ float bin_width(float mn, float mx, int B) {
+  return __fdiv_rn(__fsub_rn(mx, mn), (float)B);
+}
+__device__ __forceinline__ float boundary(float mn, float w, int j) {
+  return __fadd_rn(mn, __fmul_rn((float)j, w));
+}
+// The arithmetic estimate floor((v-min)/w) lands within one bin of the exact
+// upper-bound count for well-spread ranges; the two loops correct it against
+// the stored-boundary definition exactly (they run more than once only when
+// the range is a few ulps wide and boundaries coincide).
+__device__ __forceinline__ int bin_of(float v, float mn, float w, float inv_w, int B) {
+  if (w == 0.0f) return B - 1;  // every boundary equals min <= v
+  const float q = floorf(__fmul_rn(__fsub_rn(v, mn), inv_w));
+  int b = (q >= 0.0f) ? ((q < (float)(B - 1)) ? (int)q : (B - 1)) : 0;
+  while (b > 0 && v < boundary(mn, w, b)) --b;
+  while (b < B - 1 && boundary(mn, w, b + 1) <= v) ++b;
+  return b;
+}
+
+// Gini decrease of a candidate with left class counts L (node counts N):
+// sum_c D_c^2 / (n^2 nL nR), D_c = n L_c - N_c nL exact in int64.
+// Float version: a comparison key only (the n^2 factor is dropped); its
+// relative error is at most (C+6) 2^-24 to first order.
+__device__ __forceinline__ float gain32(const int* L, const int* N, int C, int64_t n, int64_t nL) {
+  float num = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) {
+    if (c < C) {
+      const long long D = n * (long long)L[c] - (long long)N[c] * nL;
+      const float fd = __ll2float_rn(D);
+      num = __fadd_rn(num, __fmul_rn(fd, fd));
+    }
+  }
+  const float den = __fmul_rn(__ll2float_rn(nL), __ll2float_rn(n - nL));
+  return __fdiv_rn(num, den);
+}
+
+// Double version: the exact expression of the definition, one IEEE operation
+// at a time: num = sum_c D_c*D_c (class order), g = num/(nL*nR), g = g/(n*n).
+__device__ __forceinline__ double gain64(const int* L, const int* N, int C, int64_t n, int64_t nL) {
+  double num = 0.0;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) {
+    if (c < C) {
+      const long long D = n * (long long)L[c] - (long long)N[c] * nL;
+      const double dd = __ll2double_rn(D);
+      num = __dadd_rn(num, __dmul_rn(dd, dd));
+    }
+  }
+  const double g = __ddiv_rn(num, __dmul_rn(__ll2double_rn(nL), __ll2double_rn(n - nL)));
+  return __ddiv_rn(g, __dmul_rn(__ll2double_rn(n), __ll2double_rn(n)));
+}
+
+// Exact-path threshold between consecutive distinct values a < b.
+__device__ __forceinline__ float midpoint(float a, float b) {
+  float t = __fadd_rn(a, __fmul_rn(0.5f, __fsub_rn(b, a)));
+  if (!(a < t) || !(t <= b)) t = b;
+  return t;
+}
+
+// splitmix64 (Steele, Lea & Flood 2014).
+__device__ __forceinline__ uint64_t sm64_next(uint64_t& s) {
+  uint64_t z = (s += kGamma);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t sm64(uint64_t x) {
+  uint64_t s = x;
+  return sm64_next(s);
+}
+
+// ---- warp helpers ---------------------------------------------------------
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// A candidate of the double re-score, ordered by (gain desc, proj asc, cand asc).
+struct Cand {
+  double g;
+  int proj;
+  int cand;
+};
+__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
+  if (a.g != b.g) return a.g > b.g;
+  if (a.proj != b.proj) return a.proj < b.proj;
+  return a.cand < b.cand;
+}
+__device__ __forceinline__ Cand shfl_cand(const Cand& c, int src) {
+  Cand r;
+  r.g = __shfl_sync(0xffffffffu, c.g, src);
+  r.proj = __shfl_sync(0xffffffffu, c.proj, src);
+  r.cand = __shfl_sync(0xffffffffu, c.cand, src);
+  return r;
+}
+__device__ __forceinline__ Cand warp_best(Cand c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Cand d;
+    d.g = __shfl_xor_sync(0xffffffffu, c.g, o);
+    d.proj = __shfl_xor_sync(0xffffffffu, c.proj, o);
+    d.cand = __shfl_xor_sync(0xffffffffu, c.cand, o);
+    if (better(d, c)) c = d;
+  }
+  return c;
+}
+
+}  // namespace sof

@@ -1,0 +1,225 @@
+// so_internal.h -- host-side interface between the C ABI layer (so_api.cu) and
+// the kernels (so_kernels.cu).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/soforest.h"
+
+namespace sof {
+
+constexpr int kMaxClasses = 8;     // labels in [0, 8)
+constexpr int kMaxBins = 256;      // equal-width bins per projection
+constexpr int kMaxCap = 32;        // non-zeros per projection row
+constexpr int kMaxProj = 1024;     // projections per node
+constexpr int kMaxSortBelow = 2048;  // largest exact-path node + 1
+
+// 4-lane int64 vector carried through the generic device scans.
+struct V4 {
+  long long x, y, z, w;
+};
+
+struct DatasetView {
+  const float* X;
+  int64_t n;
+  int64_t ld;
+  const uint8_t* y;
+  int32_t d;
+  int32_t C;
+};
+
+// Projection rows q = node*P + p: features feat[beg[q] .. end[q]).
+// CSR input: beg = ptr, end = ptr + 1.  Sampled slots: beg[q] = q*cap.
+struct ProjView {
+  const int32_t* beg;
+  const int32_t* end;
+  const int32_t* feat;
+  const int8_t* sign;
+  int32_t P;
+};
+
+// Bump allocator over one device buffer (256-byte aligned pieces).
+struct Carver {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  bool dry = false;  // sizing pass: count only
+  template <typename T>
+  T* take(size_t count) {
+    const size_t off = (used + 255) & ~size_t(255);
+    const size_t bytes = count * sizeof(T);
+    used = off + bytes;
+    if (dry || base == nullptr) return nullptr;
+    if (used > cap) return nullptr;
+    return reinterpret_cast<T*>(base + off);
+  }
+  bool ok() const { return dry || used <= cap; }
+};
+
+// Histogram-path work decomposition (chosen by the host; the autotuner may
+// change them).
+struct HistTuning {
+  int32_t chunk = 16384;  // samples per work item (S)
+  int32_t pgroup = 8;     // projections per work item (one warp each)
+};
+
+// Everything one batched split search needs.
+struct SearchArgs {
+  DatasetView ds;
+  const int32_t* idx = nullptr;
+  int64_t n_total = 0;
+  const int64_t* node_off = nullptr;  // device [m+1]
+  int32_t m = 0;
+  ProjView pv{};
+  int32_t B = 256;
+  int32_t T = 1024;
+  int32_t hist_only = 0;
+  float eps = 4e-6f;
+  so_split* out = nullptr;          // device [m]
+  int64_t* left_counts = nullptr;   // device [m*C] or null
+  // inspection outputs (so_histograms): all nodes forced onto the histogram path
+  float* minmax_out = nullptr;
+  int32_t* hist_out = nullptr;
+  float* gain32_out = nullptr;
+  HistTuning tune{};
+};
+
+// Device scratch of one search (carved from a workspace).
+struct SearchScratch {
+  V4* plan_total = nullptr;     // [1]: x=m_hist, y=m_sort, z=n_items
+  V4* tiles = nullptr;          // scan tile sums
+  int32_t* hist_nodes = nullptr;
+  int32_t* sort_nodes = nullptr;
+  int64_t* item_off = nullptr;
+  uint32_t* mm_keys = nullptr;  // [m_hist_cap*P*2]
+  float* max32 = nullptr;       // [m_hist_cap*P]
+  int32_t* node_counts = nullptr;  // [m_hist_cap*C]
+  int32_t* hist = nullptr;      // [m_hist_cap*P*B*C]
+  int32_t* err = nullptr;       // [1]
+  int64_t m_hist_cap = 0;
+};
+
+// Carves a SearchScratch (dry run gives the size).
+void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int32_t P, int32_t C,
+                  int32_t B, int32_t T, int32_t hist_only);
+
+// Records a CUDA event pair around a launch group when profiling is on, and
+// counts its kernel launches.
+class ProfScope {
+ public:
+  ProfScope(const char* name, cudaStream_t st, int launches = 1);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  int stage_ = -1;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+struct DeviceInfo {
+  int device = 0;
+  int num_sms = 148;
+};
+const DeviceInfo& device_info();
+
+cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStream_t st);
+
+// ---- partition ------------------------------------------------------------
+// Per-node instruction for the batched stable partition.
+enum PartMode : int32_t { PART_DROP = 0, PART_SPLIT = 1, PART_COPY = 2 };
+struct PartNode {
+  int64_t beg, end;        // segment in idx_in
+  int64_t ones_prefix;     // number of flag-1 elements before beg (whole level)
+  int64_t ones;            // flag-1 elements of this node (left size, or size for COPY)
+  int64_t dst_one;         // destination of the flag-1 part, -1 = drop
+  int64_t dst_zero;        // destination of the flag-0 part, -1 = drop
+  int64_t feat_off;        // projection row start in (feat, sign)
+  float thr;
+  int32_t nnz;
+  int32_t mode;
+  int32_t pad;
+};
+
+struct PartArgs {
+  DatasetView ds;
+  const int32_t* idx_in;
+  int32_t* idx_out;
+  int64_t n;                 // elements of the level
+  const int64_t* node_off;   // [m+1] segment starts (device), node_off[m] = n
+  int32_t m;
+  const PartNode* nodes;     // [m]
+  const int32_t* feat;
+  const int8_t* sign;
+  uint8_t* flags;            // [n]
+  int64_t* tile_cnt;         // [tiles]
+  int64_t* ones_total;       // [1] out: all flag-1 elements
+  int64_t n_out;             // length of idx_out (writes outside are refused)
+  int32_t* err;
+  PartNode* fix_node;        // single-node form: its flag-1 count is only known
+                             // after the flags are counted; set it then
+};
+int64_t part_tiles(int64_t n);
+cudaError_t launch_partition(const PartArgs& a, cudaStream_t st);
+
+// PartNode for the batch API / single-node API from split records.
+cudaError_t launch_part_nodes_from_splits(const int64_t* node_off, int32_t m, const so_split* splits,
+                                          const ProjView pv, PartNode* nodes, V4* tiles,
+                                          V4* total, cudaStream_t st);
+// Single node with a given projection: ones = computed on device.
+cudaError_t launch_part_single(int64_t n, int32_t nnz, float thr, PartNode* node,
+                               int64_t* node_off, cudaStream_t st);
+cudaError_t launch_fill_off(int64_t* off, int64_t n, cudaStream_t st);
+cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, float* gain_tmp,
+                                cudaStream_t st);
+// scan tile sums needed for n elements (tile = 2048 elements)
+inline int64_t scan_tiles_for_host(int64_t n) { return (n + 2047) / 2048 + 1; }
+
+// ---- sampler ----------------------------------------------------------------
+cudaError_t launch_sample(int32_t m, const uint64_t* keys, int32_t P, int32_t d, double lambda,
+                          int32_t cap, int32_t* nnz, int32_t* feat, int8_t* sign, int32_t* beg,
+                          int32_t* end, cudaStream_t st);
+
+// ---- tree level machinery ---------------------------------------------------
+struct TreeDev {
+  int32_t *left, *right, *depth, *leaf_class, *proj_nnz, *feat, *cand;
+  int8_t *sign, *path;
+  float* threshold;
+  int64_t *n_samples, *class_counts;
+  double* gain;
+  int32_t cap, C;
+};
+
+struct Frontier {
+  int64_t* off;      // [M+1]
+  uint64_t* key;     // [M]
+  int32_t* id;       // [M]
+  int32_t* depth;    // [M]
+  int32_t* counts;   // [M*C]
+};
+
+struct LevelStats {  // device-resident, read by the host once per level
+  long long m_next;
+  long long n_next;
+  long long new_nodes;
+  int err;
+  int pad;
+};
+
+cudaError_t launch_tree_root(const DatasetView ds, const int32_t* root_idx, int64_t n_root,
+                             uint64_t root_key, int32_t max_depth, TreeDev t, Frontier f,
+                             LevelStats* stats, cudaStream_t st);
+// Copies each searched node's winning projection (from sampled slots) and
+// split fields into the tree records.
+cudaError_t launch_tree_record_splits(int32_t j0, int32_t mb, const Frontier f, const so_split* splits,
+                                      const int32_t* snnz, const int32_t* sfeat, const int8_t* ssign,
+                                      int32_t P, int32_t cap, TreeDev t, cudaStream_t st);
+cudaError_t launch_tree_level(int32_t m, const Frontier cur, Frontier nxt, const so_split* splits,
+                              const int64_t* left_counts, int32_t max_depth, int64_t node_base_next,
+                              TreeDev t, PartNode* pnodes, V4* tiles, V4* total, LevelStats* stats,
+                              cudaStream_t st);
+
+}  // namespace sof

@@ -1,0 +1,338 @@
+"""Thin Python binding of the C ABI in include/soforest.h.
+
+Argument marshalling only: every step of the split search runs in the CUDA
+library (lib/libsoforest.so).  Device memory and streams come from PyTorch.
+There is no fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsoforest.so")
+
+SO_OK, SO_EINVAL, SO_ENOMEM, SO_ECUDA, SO_ETIMEOUT, SO_EINTERNAL = range(6)
+
+
+class SoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"soforest status {status}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------- C structs
+class so_dataset(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("ld", C.c_int64),
+                ("y", C.c_void_p), ("n_classes", C.c_int32)]
+
+
+class so_projs(C.Structure):
+    _fields_ = [("n_proj", C.c_int32), ("ptr", C.c_void_p), ("feat", C.c_void_p), ("sign", C.c_void_p)]
+
+
+class so_split_params(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("sort_below", C.c_int32), ("hist_only", C.c_int32),
+                ("rescore_rel_eps", C.c_float)]
+
+
+class so_split(C.Structure):
+    _fields_ = [("valid", C.c_int32), ("proj", C.c_int32), ("path", C.c_int32), ("cand", C.c_int32),
+                ("threshold", C.c_float), ("gain", C.c_double), ("n_left", C.c_int64),
+                ("n_right", C.c_int64)]
+
+
+class so_tree_params(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("sort_below", C.c_int32), ("hist_only", C.c_int32),
+                ("rescore_rel_eps", C.c_float), ("n_proj", C.c_int32), ("lambda_", C.c_double),
+                ("nnz_cap", C.c_int32), ("seed", C.c_uint64), ("tree_id", C.c_int32),
+                ("max_depth", C.c_int32)]
+
+
+class so_tree(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_classes", C.c_int32), ("cap", C.c_int32),
+                ("left", C.POINTER(C.c_int32)), ("right", C.POINTER(C.c_int32)),
+                ("depth", C.POINTER(C.c_int32)), ("leaf_class", C.POINTER(C.c_int32)),
+                ("proj_nnz", C.POINTER(C.c_int32)), ("feat", C.POINTER(C.c_int32)),
+                ("cand", C.POINTER(C.c_int32)), ("sign", C.POINTER(C.c_int8)),
+                ("path", C.POINTER(C.c_int8)), ("threshold", C.POINTER(C.c_float)),
+                ("n_samples", C.POINTER(C.c_int64)), ("class_counts", C.POINTER(C.c_int64)),
+                ("gain", C.POINTER(C.c_double))]
+
+
+class so_profile_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+# numpy view of an so_split array (48 bytes per record)
+SPLIT_DTYPE = np.dtype([("valid", "<i4"), ("proj", "<i4"), ("path", "<i4"), ("cand", "<i4"),
+                        ("threshold", "<f4"), ("_pad", "<i4"), ("gain", "<f8"),
+                        ("n_left", "<i8"), ("n_right", "<i8")])
+assert SPLIT_DTYPE.itemsize == C.sizeof(so_split) == 48
+
+_V, _P, _I32, _I64, _U64, _F, _D, _SZ = (C.c_void_p, C.POINTER, C.c_int32, C.c_int64, C.c_uint64,
+                                         C.c_float, C.c_double, C.c_size_t)
+
+_SIGS = {
+    "so_split_search": (_I32, [C.POINTER(so_dataset), _V, _I64, C.POINTER(so_projs),
+                               C.POINTER(so_split_params), C.POINTER(so_split), _V, _V, _SZ, _V]),
+    "so_split_search_batch": (_I32, [C.POINTER(so_dataset), _V, _I64, _V, _I32, C.POINTER(so_projs),
+                                     C.POINTER(so_split_params), _V, _V, _V, _SZ, _V]),
+    "so_split_search_ws_bytes": (_SZ, [_I32, _I64, _I32, _I32, C.POINTER(so_split_params)]),
+    "so_partition": (_I32, [C.POINTER(so_dataset), _V, _I64, _V, _V, _I32, _F, C.POINTER(C.c_int64), _V]),
+    "so_partition_batch": (_I32, [C.POINTER(so_dataset), _V, _V, _I64, _V, _I32, C.POINTER(so_projs),
+                                  _V, _V]),
+    "so_sample_projections": (_I32, [_I32, _V, _I32, _I32, _D, _I32, _V, _V, _V, _V]),
+    "so_histograms": (_I32, [C.POINTER(so_dataset), _V, _I64, _V, _I32, C.POINTER(so_projs), _I32,
+                             _V, _V, _V, _V]),
+    "so_train_tree": (_I32, [C.POINTER(so_dataset), _V, _I64, C.POINTER(so_tree_params),
+                             C.POINTER(so_tree), _V]),
+    "so_tree_free": (None, [C.POINTER(so_tree)]),
+    "so_autotune": (_I32, [C.POINTER(so_dataset), _I32, C.POINTER(so_split_params), _V]),
+    "so_last_error": (C.c_char_p, []),
+    "so_shutdown": (None, []),
+    "so_version": (C.c_char_p, []),
+    "so_profile_enable": (None, [_I32]),
+    "so_profile_read": (_I32, [C.POINTER(so_profile_entry), _I32]),
+    "so_launch_count": (_I64, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libsoforest.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2603_00326_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != SO_OK:
+        raise SoError(status, lib().so_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+# ---------------------------------------------------------------- wrappers
+@dataclasses.dataclass
+class DeviceDataset:
+    """X: cuda float32 [d, n] (row f holds feature f), y: cuda uint8 [n]."""
+    X: "object"
+    y: "object"
+    n_classes: int
+
+    def c(self) -> so_dataset:
+        X = self.X
+        assert X.is_cuda and X.dtype.__str__() == "torch.float32" and X.dim() == 2
+        assert X.stride(1) == 1
+        return so_dataset(X.data_ptr(), X.shape[1], X.shape[0], X.stride(0), self.y.data_ptr(),
+                          self.n_classes)
+
+
+@dataclasses.dataclass
+class DeviceProjs:
+    """CSR projection rows on the device: ptr int32 [rows+1], feat int32, sign int8."""
+    n_proj: int
+    ptr: "object"
+    feat: "object"
+    sign: "object"
+
+    def c(self) -> so_projs:
+        return so_projs(self.n_proj, self.ptr.data_ptr(), self.feat.data_ptr(), self.sign.data_ptr())
+
+
+def split_params(n_bins=256, sort_below=1024, hist_only=False, rescore_rel_eps=0.0) -> so_split_params:
+    return so_split_params(n_bins, sort_below, 1 if hist_only else 0, rescore_rel_eps)
+
+
+def so_version() -> str:
+    return lib().so_version().decode()
+
+
+def so_last_error() -> str:
+    return lib().so_last_error().decode()
+
+
+def so_shutdown():
+    lib().so_shutdown()
+
+
+def so_launch_count() -> int:
+    return int(lib().so_launch_count())
+
+
+def so_profile_enable(on: bool):
+    lib().so_profile_enable(1 if on else 0)
+
+
+def so_profile_read() -> dict:
+    arr = (so_profile_entry * 64)()
+    k = lib().so_profile_read(arr, 64)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(k)}
+
+
+def so_split_search(ds: DeviceDataset, idx, projs: DeviceProjs, params: so_split_params,
+                    workspace=None, stream=None):
+    """One node.  Returns (so_split, left_counts numpy int64[C])."""
+    out = so_split()
+    lc = np.zeros(8, dtype=np.int64)
+    d = ds.c()
+    p = projs.c()
+    n = 0 if idx is None else int(idx.numel())
+    _check(lib().so_split_search(C.byref(d), _ptr(idx), n, C.byref(p), C.byref(params), C.byref(out),
+                                 lc.ctypes.data_as(C.c_void_p), _ptr(workspace),
+                                 0 if workspace is None else workspace.numel() * workspace.element_size(),
+                                 _stream(stream)))
+    return out, lc[:ds.n_classes].copy()
+
+
+def so_split_search_ws_bytes(m, n_total, n_proj, n_classes, params) -> int:
+    return int(lib().so_split_search_ws_bytes(m, n_total, n_proj, n_classes, C.byref(params)))
+
+
+def so_split_search_batch(ds: DeviceDataset, idx, node_off, projs: DeviceProjs, params: so_split_params,
+                          out=None, left_counts=None, workspace=None, stream=None):
+    """m nodes (node_off: cuda int64 [m+1]).  Returns (out uint8 tensor [m*48], left_counts int64 [m*C])."""
+    import torch
+    m = int(node_off.numel()) - 1
+    dev = idx.device
+    if out is None:
+        out = torch.empty(m * SPLIT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    if left_counts is None:
+        left_counts = torch.empty(m * ds.n_classes, dtype=torch.int64, device=dev)
+    d = ds.c()
+    p = projs.c()
+    _check(lib().so_split_search_batch(
+        C.byref(d), _ptr(idx), int(idx.numel()), _ptr(node_off), m, C.byref(p), C.byref(params),
+        _ptr(out), _ptr(left_counts), _ptr(workspace),
+        0 if workspace is None else workspace.numel() * workspace.element_size(), _stream(stream)))
+    return out, left_counts
+
+
+def splits_to_numpy(out) -> np.ndarray:
+    return out.cpu().numpy().view(SPLIT_DTYPE)
+
+
+def so_partition(ds: DeviceDataset, idx, feat, sign, threshold: float, stream=None) -> int:
+    d = ds.c()
+    nl = C.c_int64(0)
+    _check(lib().so_partition(C.byref(d), _ptr(idx), int(idx.numel()), _ptr(feat), _ptr(sign),
+                              int(feat.numel()), C.c_float(threshold), C.byref(nl), _stream(stream)))
+    return int(nl.value)
+
+
+def so_partition_batch(ds: DeviceDataset, idx_in, idx_out, node_off, projs: DeviceProjs, splits,
+                       stream=None):
+    d = ds.c()
+    p = projs.c()
+    _check(lib().so_partition_batch(C.byref(d), _ptr(idx_in), _ptr(idx_out), int(idx_in.numel()),
+                                    _ptr(node_off), int(node_off.numel()) - 1, C.byref(p), _ptr(splits),
+                                    _stream(stream)))
+
+
+def so_sample_projections(keys, n_proj: int, d: int, lam: float, cap: int, stream=None):
+    """keys: cuda int64 [m] (bit patterns of uint64 keys).  Returns (nnz, feat, sign) slot tensors."""
+    import torch
+    m = int(keys.numel())
+    nnz = torch.empty(m * n_proj, dtype=torch.int32, device=keys.device)
+    feat = torch.zeros(m * n_proj * cap, dtype=torch.int32, device=keys.device)
+    sign = torch.zeros(m * n_proj * cap, dtype=torch.int8, device=keys.device)
+    _check(lib().so_sample_projections(m, _ptr(keys), n_proj, d, lam, cap, _ptr(nnz), _ptr(feat),
+                                       _ptr(sign), _stream(stream)))
+    return nnz, feat, sign
+
+
+def so_histograms(ds: DeviceDataset, idx, node_off, projs: DeviceProjs, n_bins: int, want_gains=False,
+                  stream=None):
+    """Histogram stage of m nodes.  Returns (minmax [m,P,2], hist [m,P,B,C], gains [m,P,B-1] or None)."""
+    import torch
+    m = int(node_off.numel()) - 1
+    P, Cc = projs.n_proj, ds.n_classes
+    dev = idx.device
+    mm = torch.zeros((m, P, 2), dtype=torch.float32, device=dev)
+    hist = torch.zeros((m, P, n_bins, Cc), dtype=torch.int32, device=dev)
+    gains = torch.zeros((m, P, n_bins - 1), dtype=torch.float32, device=dev) if want_gains else None
+    d = ds.c()
+    p = projs.c()
+    _check(lib().so_histograms(C.byref(d), _ptr(idx), int(idx.numel()), _ptr(node_off), m, C.byref(p),
+                               n_bins, _ptr(mm), _ptr(hist), _ptr(gains), _stream(stream)))
+    return mm, hist, gains
+
+
+@dataclasses.dataclass
+class Tree:
+    n_nodes: int
+    left: np.ndarray
+    right: np.ndarray
+    depth: np.ndarray
+    leaf_class: np.ndarray
+    proj_nnz: np.ndarray
+    feat: np.ndarray
+    sign: np.ndarray
+    cand: np.ndarray
+    path: np.ndarray
+    threshold: np.ndarray
+    n_samples: np.ndarray
+    class_counts: np.ndarray
+    gain: np.ndarray
+
+    FIELDS = ("left", "right", "depth", "leaf_class", "proj_nnz", "feat", "sign", "cand",
+              "path", "threshold", "n_samples", "class_counts", "gain")
+
+
+def tree_params(n_proj, lam, cap, n_bins=256, sort_below=1024, hist_only=False, seed=0, tree_id=0,
+                max_depth=-1, rescore_rel_eps=0.0) -> so_tree_params:
+    return so_tree_params(n_bins, sort_below, 1 if hist_only else 0, rescore_rel_eps, n_proj, lam, cap,
+                          seed & 0xFFFFFFFFFFFFFFFF, tree_id, max_depth)
+
+
+def so_train_tree(ds: DeviceDataset, root_idx, params: so_tree_params, stream=None) -> Tree:
+    d = ds.c()
+    t = so_tree()
+    _check(lib().so_train_tree(C.byref(d), _ptr(root_idx), int(root_idx.numel()), C.byref(params),
+                               C.byref(t), _stream(stream)))
+    try:
+        m, cap, Cc = int(t.n_nodes), int(t.cap), int(t.n_classes)
+
+        def arr(ptr, count, dtype):
+            return np.ctypeslib.as_array(ptr, shape=(count,)).astype(dtype, copy=True)
+
+        return Tree(
+            n_nodes=m, left=arr(t.left, m, np.int32), right=arr(t.right, m, np.int32),
+            depth=arr(t.depth, m, np.int32), leaf_class=arr(t.leaf_class, m, np.int32),
+            proj_nnz=arr(t.proj_nnz, m, np.int32),
+            feat=arr(t.feat, m * cap, np.int32).reshape(m, cap),
+            sign=arr(t.sign, m * cap, np.int8).reshape(m, cap),
+            cand=arr(t.cand, m, np.int32), path=arr(t.path, m, np.int8),
+            threshold=arr(t.threshold, m, np.float32), n_samples=arr(t.n_samples, m, np.int64),
+            class_counts=arr(t.class_counts, m * Cc, np.int64).reshape(m, Cc),
+            gain=arr(t.gain, m, np.float64))
+    finally:
+        lib().so_tree_free(C.byref(t))
+
+
+def so_autotune(ds: DeviceDataset, n_proj: int, params: so_split_params, stream=None) -> so_split_params:
+    d = ds.c()
+    _check(lib().so_autotune(C.byref(d), n_proj, C.byref(params), _stream(stream)))
+    return params
