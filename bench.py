@@ -183,7 +183,7 @@ def run_ours(args):
     idx = idx_h.to(dev)
     ptr, feat, sign = ptr_h.to(dev), feat_h.to(dev), sign_h.to(dev)
     ds = S.DeviceDataset(X, y, C)
-    pj = S.DeviceProjs(P, ptr, feat, sign)
+    pj = S.DeviceProjs(P, ptr, feat, sign, int(np.diff(pr.ptr).max()))
     off = torch.tensor([0, n], dtype=torch.int64, device=dev)
     prm = S.split_params(p["n_bins"], 0, True)
     ws = torch.empty(S.so_split_search_ws_bytes(1, n, P, C, prm), dtype=torch.uint8, device=dev)

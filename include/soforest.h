@@ -73,6 +73,9 @@ typedef struct {
     const int32_t *ptr;    /* [rows + 1] */
     const int32_t *feat;   /* [ptr[rows]] */
     const int8_t *sign;    /* [ptr[rows]] */
+    int32_t max_nnz;       /* upper bound of every row length (selects the kernel
+                              variant), 1..32; 0 = unknown, taken as 32.  A row
+                              longer than this marks its node malformed. */
 } so_projs;
 
 /* Split-search parameters.

@@ -129,6 +129,7 @@ so_status check_projs(const so_projs* pr) {
   if (!pr) return fail(SO_EINVAL, "projs is NULL");
   if (pr->n_proj < 1 || pr->n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj=%d outside 1..1024", pr->n_proj);
   if (!pr->ptr || !pr->feat || !pr->sign) return fail(SO_EINVAL, "projection arrays are NULL");
+  if (pr->max_nnz < 0 || pr->max_nnz > kMaxCap) return fail(SO_EINVAL, "max_nnz=%d outside 0..32", pr->max_nnz);
   return SO_OK;
 }
 
@@ -149,6 +150,10 @@ DatasetView view_of(const so_dataset* ds) {
   v.d = ds->d;
   v.C = ds->n_classes;
   return v;
+}
+
+int32_t projs_max_nnz(const so_projs* pr) {
+  return (pr->max_nnz >= 1 && pr->max_nnz <= kMaxCap) ? pr->max_nnz : kMaxCap;
 }
 
 ProjView csr_view(const so_projs* pr) {
@@ -255,6 +260,7 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     a.T = params->sort_below;
     a.hist_only = params->hist_only ? 1 : 0;
     a.eps = effective_eps(params->rescore_rel_eps, C);
+    a.max_nnz = projs_max_nnz(projs);
     a.out = out_dev;
     a.left_counts = left_counts_dev;
     SO_CK(launch_search(a, s, cs));
@@ -306,6 +312,7 @@ so_status so_split_search(const so_dataset* ds, const int32_t* idx, int64_t n_no
     a.T = params->sort_below;
     a.hist_only = params->hist_only ? 1 : 0;
     a.eps = effective_eps(params->rescore_rel_eps, C);
+    a.max_nnz = projs_max_nnz(projs);
     a.out = out_dev;
     a.left_counts = lc;
     SO_CK(launch_search(a, s, cs));
@@ -491,6 +498,7 @@ so_status so_histograms(const so_dataset* ds, const int32_t* idx, int64_t n_tota
     a.B = n_bins;
     a.T = 0;
     a.hist_only = 1;
+    a.max_nnz = projs_max_nnz(projs);
     a.minmax_out = minmax_dev;
     a.hist_out = hist_dev;
     a.gain32_out = gain32_dev;
@@ -638,6 +646,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
         a.T = T;
         a.hist_only = HO;
         a.eps = eps;
+        a.max_nnz = cap;
         a.out = spl + j0;
         a.left_counts = lc + j0 * C;
         SO_CK(launch_search(a, ss, cs));

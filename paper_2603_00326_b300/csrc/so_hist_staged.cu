@@ -1,0 +1,669 @@
+// so_hist_staged.cu -- staged-tile kernels of the histogram path (sm_103a).
+//
+// A work item is (histogram node, sample chunk, projection group).  The
+// item's projections use U distinct features; for each tile of St samples
+// the CTA stages those U feature columns once in shared memory (one global
+// read per (sample, feature)), then every projection of the group is
+// evaluated from shared memory: one warp per projection, each lane a pair of
+// consecutive samples, packed FP32x2 arithmetic.  Projection groups are
+// formed on the device so that U stays within the tile budget.
+//
+//   k_groups       per histogram node: greedy grouping of its projections
+//   k_mm_staged    per item: min / max of every projection (Section 3 step 2)
+//   k_hist_staged  per item: equal-width bins and class counts in shared
+//                  memory, flushed with integer atomics (Section 3 step 2)
+//
+// Exact bins without search loops.  With W = (max-min)/B and
+// t_j = min + j*W (float), bin(v) = #{j in 1..B-1 : t_j <= v}.  Let
+// e = v*inv_w + c with c = fl(fl(-min*inv_w) - 0.75) (one fused rounding) and
+// q = round_half_even(e) (by adding 1.5*2^23).  When max(|min|,|max|) <= 2^18 W
+// the combined rounding errors of e and of the t_j are below 1/4 bin, which
+// gives bin(v) in {q, q+1}: bin(v) = q + [t_{q+1} <= v], with t_{q+1}
+// computed exactly as the definition states.  q = -1 resolves to bin 0
+// (t_0 = min <= v); q+1 = B lands in a spare bin merged into bin B-1 on flush.
+// Projections outside that condition take the exact estimate-and-correct rule.
+#include <climits>
+
+#include "so_device.cuh"
+#include "so_internal.h"
+#include "so_scan.cuh"
+
+namespace sof {
+
+constexpr int kStThreads = 512;          // threads of the staged kernels (16 warps)
+constexpr int kStWarps = kStThreads / 32;
+constexpr int kStEpt = 32;               // staged elements per thread per tile (registers)
+constexpr int kStUMax = kStThreads * kStEpt / 64;  // rows of a tile at St = 64 -> 256
+constexpr int kStMaxWords = 2048;        // feature bitmap words (d <= 65536)
+constexpr int kMmPPW = 16;               // min/max: projections per warp
+constexpr int kMmGroup = kStWarps * kMmPPW;  // 256 projections per min/max group
+constexpr float kMagic = 12582912.0f;    // 1.5 * 2^23
+constexpr float kCondLimit = 262144.0f;  // 2^18
+
+// ---- packed FP32x2 (sm_100+ PTX) ------------------------------------------
+__device__ __forceinline__ unsigned long long as_u64(float2 a) {
+  return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+}
+__device__ __forceinline__ float2 as_f2(unsigned long long u) {
+  return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)), "l"(as_u64(c)));
+  return as_f2(d);
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)));
+  return as_f2(d);
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)));
+  return as_f2(d);
+}
+
+// ---- staged plan ------------------------------------------------------------
+struct StagedPlan {
+  const V4* plan_total;     // x = m_hist
+  const int32_t* hist_nodes;
+  const int64_t* node_off;
+  const int32_t* ng;        // [m_hist_cap] groups per node
+  const int32_t* gstart;    // [m_hist_cap][P+1] first projection of each group
+  const int64_t* item_off;  // [m_hist_cap] first item of each node
+  const V4* item_total;     // lane: items of this kernel
+  int lane;                 // 0: min/max items (x), 1: histogram items (y)
+  int64_t S;                // samples per chunk
+};
+
+__device__ __forceinline__ int64_t items_total(const StagedPlan& sp) {
+  const V4 t = *sp.item_total;
+  return sp.lane == 0 ? t.x : t.y;
+}
+
+struct ItemPos {
+  int64_t h;
+  int j;
+  int64_t beg, end;
+  int p0, np;
+};
+
+__device__ __forceinline__ ItemPos decode_item(const StagedPlan& sp, int64_t t, int P) {
+  ItemPos r;
+  const int64_t m_hist = sp.plan_total->x;
+  int64_t lo = 0, hi = m_hist - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (sp.item_off[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  r.h = lo;
+  r.j = sp.hist_nodes[lo];
+  const int ng = sp.ng[lo];
+  const int64_t local = t - sp.item_off[lo];
+  const int64_t chunk = local / ng;
+  const int g = (int)(local - chunk * ng);
+  const int32_t* gs = sp.gstart + lo * (int64_t)(P + 1);
+  r.p0 = gs[g];
+  r.np = gs[g + 1] - gs[g];
+  const int64_t nb = sp.node_off[r.j], ne = sp.node_off[r.j + 1];
+  r.beg = nb + chunk * sp.S;
+  r.end = min(ne, r.beg + sp.S);
+  return r;
+}
+
+// ---- feature bitmap -> tile rows --------------------------------------------
+// Marks the features of projections [p0, p0+np) of node j, assigns rows in
+// ascending feature order and returns U.  The caller syncs before use.
+__device__ __forceinline__ int build_rows(const ProjView& pv, int64_t qbase, int np, int d, uint32_t* s_bits,
+                                          int* s_wpre, int* s_rowfeat, int* s_misc) {
+  const int nw = (d + 31) >> 5;
+  for (int w = threadIdx.x; w < nw; w += kStThreads) s_bits[w] = 0u;
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += kStThreads) {
+    const int rb = pv.beg[qbase + p];
+    int k = pv.end[qbase + p] - rb;
+    k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
+    for (int jj = 0; jj < k; ++jj) {
+      int f = pv.feat[rb + jj];
+      f = (f < 0 || f >= d) ? 0 : f;
+      atomicOr(&s_bits[f >> 5], 1u << (f & 31));
+    }
+  }
+  __syncthreads();
+  // exclusive prefix of popcounts over the words: each thread a run of words
+  const int per = (nw + kStThreads - 1) / kStThreads;
+  const int w0 = threadIdx.x * per;
+  int own = 0;
+  for (int w = w0; w < min(nw, w0 + per); ++w) own += __popc(s_bits[w]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int inc = warp_incl_scan(own, lane);
+  if (lane == 31) s_misc[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int v = lane < kStWarps ? s_misc[lane] : 0;
+    const int vi = warp_incl_scan(v, lane);
+    if (lane < kStWarps) s_misc[lane] = vi - v;
+    if (lane == kStWarps - 1) s_misc[kStWarps] = vi;
+  }
+  __syncthreads();
+  int run = s_misc[warp] + inc - own;
+  for (int w = w0; w < min(nw, w0 + per); ++w) {
+    s_wpre[w] = run;
+    run += __popc(s_bits[w]);
+  }
+  const int U = s_misc[kStWarps];
+  __syncthreads();
+  if (U <= kStUMax) {
+    for (int w = threadIdx.x; w < nw; w += kStThreads) {
+      unsigned bits = s_bits[w];
+      int r = s_wpre[w];
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        s_rowfeat[r++] = w * 32 + b;
+        bits &= bits - 1u;
+      }
+    }
+  }
+  return U;
+}
+
+__device__ __forceinline__ int row_of(int f, const uint32_t* s_bits, const int* s_wpre) {
+  return s_wpre[f >> 5] + __popc(s_bits[f >> 5] & ((1u << (f & 31)) - 1u));
+}
+
+// Projection descriptors of the group in shared memory: k, row of each
+// non-zero (ascending feature order), sign as a float multiplier.
+template <int KMAX>
+__device__ __forceinline__ void build_desc(const ProjView& pv, int64_t qbase, int np, int d, const uint32_t* s_bits,
+                                           const int* s_wpre, int* s_dk, int16_t* s_drow, float* s_dsg) {
+  for (int e = threadIdx.x; e < np * KMAX; e += kStThreads) {
+    const int p = e / KMAX, jj = e - (e / KMAX) * KMAX;
+    const int rb = pv.beg[qbase + p];
+    int k = pv.end[qbase + p] - rb;
+    k = k < 0 ? 0 : (k > KMAX ? KMAX : k);
+    if (jj == 0) s_dk[p] = k;
+    if (jj < k) {
+      int f = pv.feat[rb + jj];
+      f = (f < 0 || f >= d) ? 0 : f;
+      s_drow[p * KMAX + jj] = (int16_t)row_of(f, s_bits, s_wpre);
+      s_dsg[p * KMAX + jj] = pv.sign[rb + jj] == 1 ? 1.0f : -1.0f;
+    }
+  }
+}
+
+// ---- tile staging through registers (prefetch of the next tile) -------------
+// Thread owns tile column i = tid % St and rows tid/St + k*(NT/St).
+struct TileLoader {
+  float pre[kStEpt];
+  int sid;
+  bool valid;
+  __device__ __forceinline__ void load(const DatasetView& ds, const int32_t* __restrict__ idx, int64_t tbeg,
+                                       int64_t tend, int St, int U, const int* s_rowfeat) {
+    const int i = threadIdx.x % St;
+    const int r0 = threadIdx.x / St;
+    const int rstep = kStThreads / St;
+    const int64_t pos = tbeg + i;
+    valid = pos < tend;
+    sid = (int)safe_sample(idx[valid ? pos : tbeg], ds.n);
+#pragma unroll
+    for (int k = 0; k < kStEpt; ++k) {
+      const int r = r0 + k * rstep;
+      if (r < U) pre[k] = __ldg(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid);
+    }
+  }
+  __device__ __forceinline__ void store(float* s_tile, int St, int U) const {
+    const int i = threadIdx.x % St;
+    const int r0 = threadIdx.x / St;
+    const int rstep = kStThreads / St;
+#pragma unroll
+    for (int k = 0; k < kStEpt; ++k) {
+      const int r = r0 + k * rstep;
+      if (r < U) s_tile[r * St + i] = pre[k];
+    }
+  }
+};
+
+__device__ __forceinline__ int choose_st(int U) {
+  // U * St <= kStThreads * kStEpt, St in {64, 128, 256}
+  if (U * 256 <= kStThreads * kStEpt) return 256;
+  if (U * 128 <= kStThreads * kStEpt) return 128;
+  return 64;
+}
+
+// ---- k_groups: greedy projection groups per histogram node -------------------
+// One warp per node.  A group is closed before a projection that would push
+// its distinct features above umax or its size above pmax.
+__global__ void __launch_bounds__(128) k_groups(const V4* plan_total, const int32_t* hist_nodes, ProjView pv, int d,
+                                                int umax1, int pmax1, int umax2, int pmax2, int32_t* ng1,
+                                                int32_t* gs1, int32_t* ng2, int32_t* gs2) {
+  extern __shared__ uint32_t s_grp[];  // per warp: bitmap [nw] + set-word list [kStUMax]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (d + 31) >> 5;
+  uint32_t* bits = s_grp + warp * (nw + kStUMax);
+  uint32_t* setw = bits + nw;
+  for (int w = lane; w < nw; w += 32) bits[w] = 0u;
+  __syncwarp();
+  const int64_t m_hist = plan_total->x;
+  const int P = pv.P;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t h = gw; h < m_hist; h += nwarps) {
+    const int64_t j = hist_nodes[h];
+    for (int pass = 0; pass < 2; ++pass) {
+      const int umax = pass == 0 ? umax1 : umax2;
+      const int pmax = pass == 0 ? pmax1 : pmax2;
+      int32_t* gs = (pass == 0 ? gs1 : gs2) + h * (int64_t)(P + 1);
+      int U = 0, cnt = 0, nset = 0, g = 0;
+      if (lane == 0) gs[0] = 0;
+      for (int p = 0; p < P; ++p) {
+        const int64_t q = j * P + p;
+        const int rb = pv.beg[q];
+        int k = pv.end[q] - rb;
+        k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
+        int f = 0;
+        if (lane < k) {
+          f = pv.feat[rb + lane];
+          f = (f < 0 || f >= d) ? 0 : f;
+        }
+        bool fresh = lane < k && !(bits[f >> 5] & (1u << (f & 31)));
+        int add = __popc(__ballot_sync(0xffffffffu, fresh));
+        if (cnt > 0 && (U + add > umax || cnt + 1 > pmax)) {
+          for (int s = lane; s < nset; s += 32) bits[setw[s]] = 0u;
+          __syncwarp();
+          U = 0;
+          cnt = 0;
+          nset = 0;
+          ++g;
+          if (lane == 0) gs[g] = p;
+          fresh = lane < k;
+          add = __popc(__ballot_sync(0xffffffffu, fresh));
+        }
+        // set the bits; record words that become non-zero
+        bool newword = false;
+        if (fresh) {
+          const uint32_t old = atomicOr(&bits[f >> 5], 1u << (f & 31));
+          newword = (old == 0u);
+        }
+        // a word may be set by two lanes of the same projection; only the
+        // lane that saw it empty records it
+        const unsigned nb = __ballot_sync(0xffffffffu, newword);
+        if (newword) setw[nset + __popc(nb & ((1u << lane) - 1u))] = (uint32_t)(f >> 5);
+        nset += __popc(nb);
+        U += add;
+        ++cnt;
+        __syncwarp();
+      }
+      for (int s = lane; s < nset; s += 32) bits[setw[s]] = 0u;
+      __syncwarp();
+      if (lane == 0) {
+        gs[g + 1] = P;
+        (pass == 0 ? ng1 : ng2)[h] = g + 1;
+      }
+    }
+  }
+}
+
+// Item counts per histogram node (scan over node slots; slots >= m_hist are 0).
+struct ItemScanF {
+  const V4* plan_total;
+  const int32_t* hist_nodes;
+  const int64_t* off;
+  const int32_t* ng1;
+  const int32_t* ng2;
+  int64_t S;
+  int64_t* item_off1;
+  int64_t* item_off2;
+  __device__ V4 value(int64_t h) const {
+    if (h >= plan_total->x) return V4{0, 0, 0, 0};
+    const int j = hist_nodes[h];
+    const int64_t nv = off[j + 1] - off[j];
+    const int64_t ch = (nv + S - 1) / S;
+    return V4{ch * ng1[h], ch * ng2[h], 0, 0};
+  }
+  __device__ void apply(int64_t h, V4 ex) const {
+    if (h >= plan_total->x) return;
+    item_off1[h] = ex.x;
+    item_off2[h] = ex.y;
+  }
+};
+
+// ---- k_mm_staged: min / max -------------------------------------------------
+template <int KMAX>
+__global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, const int32_t* __restrict__ idx,
+                                                            ProjView pv, StagedPlan sp, uint32_t* mm) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  const int nw = (ds.d + 31) >> 5;
+  float* s_tile = reinterpret_cast<float*>(s_raw);                       // [kStThreads*kStEpt]
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_tile + kStThreads * kStEpt);  // [nw]
+  int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                     // [nw]
+  int* s_rowfeat = s_wpre + nw;                                          // [kStUMax]
+  int* s_dk = s_rowfeat + kStUMax;                                       // [kMmGroup]
+  float* s_dsg = reinterpret_cast<float*>(s_dk + kMmGroup);              // [kMmGroup*KMAX]
+  int16_t* s_drow = reinterpret_cast<int16_t*>(s_dsg + kMmGroup * KMAX); // [kMmGroup*KMAX]
+  __shared__ int s_misc[kStWarps + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P = pv.P;
+  const int64_t n_items = items_total(sp);
+  for (int64_t t = blockIdx.x; t < n_items; t += gridDim.x) {
+    const ItemPos it = decode_item(sp, t, P);
+    const int64_t qbase = (int64_t)it.j * P + it.p0;
+    __syncthreads();  // previous item done with shared memory
+    const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
+    build_desc<KMAX>(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_dk, s_drow, s_dsg);
+    __syncthreads();
+    float mn[kMmPPW], mx[kMmPPW];
+#pragma unroll
+    for (int i = 0; i < kMmPPW; ++i) {
+      mn[i] = INFINITY;
+      mx[i] = -INFINITY;
+    }
+    if (U <= kStUMax) {
+      const int St = choose_st(U);
+      const int64_t len = it.end - it.beg;
+      const int64_t ntile = (len + St - 1) / St;
+      TileLoader ld;
+      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat);
+      for (int64_t tt = 0; tt < ntile; ++tt) {
+        __syncthreads();
+        ld.store(s_tile, St, U);
+        __syncthreads();
+        if (tt + 1 < ntile) {
+          const int64_t nb = it.beg + (tt + 1) * St;
+          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat);
+        }
+        // positions beyond the chunk repeat the tile's first sample, so they
+        // never change a minimum or maximum
+#pragma unroll
+        for (int i = 0; i < kMmPPW; ++i) {
+          const int pl = warp * kMmPPW + i;
+          if (pl < it.np) {
+            const int k = s_dk[pl];
+            for (int ps = 0; ps < St; ps += 64) {
+              const int i0 = ps + 2 * lane;
+              float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+              for (int jj = 0; jj < KMAX; ++jj) {
+                if (jj < k) {
+                  const float2 x = *reinterpret_cast<const float2*>(s_tile + s_drow[pl * KMAX + jj] * St + i0);
+                  const float s = s_dsg[pl * KMAX + jj];
+                  acc = ffma2(make_float2(s, s), x, acc);
+                }
+              }
+              mn[i] = fminf(mn[i], fminf(acc.x, acc.y));
+              mx[i] = fmaxf(mx[i], fmaxf(acc.x, acc.y));
+            }
+          }
+        }
+      }
+    } else {
+      // direct path for wide groups: each warp gathers its projections' features
+      for (int i = 0; i < kMmPPW; ++i) {
+        const int pl = warp * kMmPPW + i;
+        if (pl >= it.np) break;
+        const int64_t q = qbase + pl;
+        const int rb = pv.beg[q];
+        int k = pv.end[q] - rb;
+        k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
+        for (int64_t e = it.beg + lane; e < it.end; e += 32) {
+          const int64_t s = safe_sample(idx[e], ds.n);
+          float acc = 0.0f;
+          for (int jj = 0; jj < k; ++jj) {
+            int f = pv.feat[rb + jj];
+            f = (f < 0 || f >= ds.d) ? 0 : f;
+            const float x = __ldg(ds.X + (int64_t)f * ds.ld + s);
+            acc = __fadd_rn(acc, pv.sign[rb + jj] == 1 ? x : -x);
+          }
+          mn[0] = fminf(mn[0], acc);
+          mx[0] = fmaxf(mx[0], acc);
+        }
+        const float a = warp_min(mn[0]), b = warp_max(mx[0]);
+        if (lane == 0) {
+          atomicMin(&mm[(it.h * P + it.p0 + pl) * 2], f2key(a));
+          atomicMax(&mm[(it.h * P + it.p0 + pl) * 2 + 1], f2key(b));
+        }
+        mn[0] = INFINITY;
+        mx[0] = -INFINITY;
+      }
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < kMmPPW; ++i) {
+      const int pl = warp * kMmPPW + i;
+      const float a = warp_min(mn[i]), b = warp_max(mx[i]);
+      if (lane == 0 && pl < it.np) {
+        atomicMin(&mm[(it.h * P + it.p0 + pl) * 2], f2key(a));
+        atomicMax(&mm[(it.h * P + it.p0 + pl) * 2 + 1], f2key(b));
+      }
+    }
+  }
+}
+
+// ---- k_hist_staged: class-count histograms -----------------------------------
+// Histogram layout in shared memory: [pl][B+1][C] int32, one spare bin per
+// projection, plus one trash histogram for padding positions.
+template <int KMAX>
+__global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, const int32_t* __restrict__ idx,
+                                                              ProjView pv, StagedPlan sp, int B, int PG,
+                                                              const uint32_t* __restrict__ mm, int32_t* hist) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  const int nw = (ds.d + 31) >> 5;
+  const int C = ds.C;
+  const int HS = (B + 1) * C;  // words per projection histogram
+  float* s_tile = reinterpret_cast<float*>(s_raw);                        // [kStThreads*kStEpt]
+  int32_t* s_hist = reinterpret_cast<int32_t*>(s_tile + kStThreads * kStEpt);  // [(PG+1)*HS]
+  int* s_y4 = s_hist + (PG + 1) * HS;                                     // [256] byte offset of the label
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_y4 + 256);             // [nw]
+  int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                      // [nw]
+  int* s_rowfeat = s_wpre + nw;                                           // [kStUMax]
+  int* s_dk = s_rowfeat + kStUMax;                                        // [PG]
+  float* s_dsg = reinterpret_cast<float*>(s_dk + 32);                     // [PG*KMAX]
+  int16_t* s_drow = reinterpret_cast<int16_t*>(s_dsg + 32 * KMAX);        // [PG*KMAX]
+  __shared__ int s_misc[kStWarps + 1];
+  __shared__ float s_bp[32][5];  // per projection: mn, W, inv_w, c, fast flag
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P = pv.P;
+  const int magic_bits = (int)__float_as_uint(kMagic);
+  const int64_t n_items = items_total(sp);
+  for (int64_t t = blockIdx.x; t < n_items; t += gridDim.x) {
+    const ItemPos it = decode_item(sp, t, P);
+    const int64_t qbase = (int64_t)it.j * P + it.p0;
+    __syncthreads();  // previous item's flush finished
+    for (int e = threadIdx.x; e < (PG + 1) * HS; e += kStThreads) s_hist[e] = 0;
+    const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
+    build_desc<KMAX>(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_dk, s_drow, s_dsg);
+    if (threadIdx.x < it.np) {
+      const int pl = threadIdx.x;
+      const float mn = key2f(mm[(it.h * P + it.p0 + pl) * 2]);
+      const float mx = key2f(mm[(it.h * P + it.p0 + pl) * 2 + 1]);
+      const float W = bin_width(mn, mx, B);
+      const float inv_w = __frcp_rn(W);
+      const float c = __fsub_rn(__fmul_rn(-mn, inv_w), 0.75f);
+      const float M = fmaxf(fabsf(mn), fabsf(mx));
+      const bool fast = W > 0.0f && isfinite(inv_w) && isfinite(c) && M <= kCondLimit * W;
+      s_bp[pl][0] = mn;
+      s_bp[pl][1] = W;
+      s_bp[pl][2] = inv_w;
+      s_bp[pl][3] = c;
+      s_bp[pl][4] = fast ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    const int64_t len = it.end - it.beg;
+    if (U <= kStUMax) {
+      const int St = choose_st(U);
+      const int64_t ntile = (len + St - 1) / St;
+      TileLoader ld;
+      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat);
+      int ylab = 0;
+      if (threadIdx.x < St) ylab = ld.valid ? (int)ds.y[ld.sid] : -1;
+      for (int64_t tt = 0; tt < ntile; ++tt) {
+        __syncthreads();
+        ld.store(s_tile, St, U);
+        if (threadIdx.x < St) {
+          // byte offset added to a projection's bin offset; padding and labels
+          // outside [0, C) go to the trash histogram
+          s_y4[threadIdx.x] = (ylab >= 0 && ylab < C) ? ylab * 4 : -1;
+        }
+        __syncthreads();
+        if (tt + 1 < ntile) {
+          const int64_t nb = it.beg + (tt + 1) * St;
+          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat);
+          if (threadIdx.x < St) ylab = ld.valid ? (int)ds.y[ld.sid] : -1;
+        }
+        for (int pl = warp; pl < it.np; pl += kStWarps) {
+          const int k = s_dk[pl];
+          const float mn = s_bp[pl][0], W = s_bp[pl][1], inv_w = s_bp[pl][2], c = s_bp[pl][3];
+          const bool fast = s_bp[pl][4] != 0.0f;
+          const int hbase4 = pl * HS * 4;                  // byte offset of the projection's histogram
+          const int trash4 = PG * HS * 4;
+          for (int ps = 0; ps < St; ps += 64) {
+            const int i0 = ps + 2 * lane;
+            float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int jj = 0; jj < KMAX; ++jj) {
+              if (jj < k) {
+                const float2 x = *reinterpret_cast<const float2*>(s_tile + s_drow[pl * KMAX + jj] * St + i0);
+                const float s = s_dsg[pl * KMAX + jj];
+                acc = ffma2(make_float2(s, s), x, acc);
+              }
+            }
+            const int2 y4 = *reinterpret_cast<const int2*>(s_y4 + i0);
+            int bx, by;
+            if (fast) {
+              const float2 e = ffma2(acc, make_float2(inv_w, inv_w), make_float2(c, c));
+              const float2 tq = fadd2(e, make_float2(kMagic, kMagic));
+              const float2 q1 = fadd2(tq, make_float2(1.0f - kMagic, 1.0f - kMagic));
+              const float2 tb = fadd2(make_float2(mn, mn), fmul2(q1, make_float2(W, W)));
+              bx = (int)__float_as_uint(tq.x) - magic_bits + (tb.x <= acc.x ? 1 : 0);
+              by = (int)__float_as_uint(tq.y) - magic_bits + (tb.y <= acc.y ? 1 : 0);
+            } else {
+              bx = bin_of(acc.x, mn, W, inv_w, B);
+              by = bin_of(acc.y, mn, W, inv_w, B);
+            }
+            // padding, labels outside [0, C) and (for non-finite input) bins
+            // outside [0, B] go to the trash histogram
+            const int ax = (y4.x >= 0 && (unsigned)bx <= (unsigned)B) ? hbase4 + bx * C * 4 + y4.x : trash4;
+            const int ay = (y4.y >= 0 && (unsigned)by <= (unsigned)B) ? hbase4 + by * C * 4 + y4.y : trash4;
+            atomicAdd(reinterpret_cast<int*>(reinterpret_cast<char*>(s_hist) + ax), 1);
+            atomicAdd(reinterpret_cast<int*>(reinterpret_cast<char*>(s_hist) + ay), 1);
+          }
+        }
+      }
+    } else {
+      // direct path for wide groups (rare): one warp per projection, gathers
+      for (int pl = warp; pl < it.np; pl += kStWarps) {
+        const int64_t q = qbase + pl;
+        const int rb = pv.beg[q];
+        int k = pv.end[q] - rb;
+        k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
+        const float mn = s_bp[pl][0], W = s_bp[pl][1], inv_w = s_bp[pl][2];
+        for (int64_t e = it.beg + lane; e < it.end; e += 32) {
+          const int64_t s = safe_sample(idx[e], ds.n);
+          float acc = 0.0f;
+          for (int jj = 0; jj < k; ++jj) {
+            int f = pv.feat[rb + jj];
+            f = (f < 0 || f >= ds.d) ? 0 : f;
+            const float x = __ldg(ds.X + (int64_t)f * ds.ld + s);
+            acc = __fadd_rn(acc, pv.sign[rb + jj] == 1 ? x : -x);
+          }
+          const int yv = ds.y[s];
+          if (yv < C) atomicAdd(&s_hist[pl * HS + bin_of(acc, mn, W, inv_w, B) * C + yv], 1);
+        }
+      }
+    }
+    __syncthreads();
+    // flush: the spare bin B folds into bin B-1
+    const int BC = B * C;
+    for (int e = threadIdx.x; e < it.np * BC; e += kStThreads) {
+      const int pl = e / BC;
+      const int r = e - pl * BC;
+      int v = s_hist[pl * HS + r];
+      if (r >= (B - 1) * C) v += s_hist[pl * HS + r + C];
+      if (v) atomicAdd(&hist[(it.h * P + it.p0 + pl) * (int64_t)BC + r], v);
+    }
+  }
+}
+
+// ---- host side ----------------------------------------------------------------
+int hist_group_size(int B, int C) {
+  // histogram shared memory <= 100 KB: (PG + 1) * (B + 1) * C * 4
+  int pg = 32;
+  while (pg > 1 && (size_t)(pg + 1) * (B + 1) * C * 4 > 100 * 1024) pg >>= 1;
+  return pg;
+}
+
+size_t mm_smem_bytes(int d, int kmax) {
+  const int nw = (d + 31) >> 5;
+  return (size_t)kStThreads * kStEpt * 4 + (size_t)nw * 8 + kStUMax * 4 + kMmGroup * 4 +
+         (size_t)kMmGroup * kmax * 6 + 64;
+}
+size_t hist_smem_bytes(int d, int kmax, int B, int C, int PG) {
+  const int nw = (d + 31) >> 5;
+  return (size_t)kStThreads * kStEpt * 4 + (size_t)(PG + 1) * (B + 1) * C * 4 + 256 * 4 + (size_t)nw * 8 +
+         kStUMax * 4 + 32 * 4 + (size_t)32 * kmax * 6 + 64;
+}
+
+bool staged_supported(int d) { return d <= kStMaxWords * 32; }
+
+void carve_staged(Carver& cv, StagedScratch& s, int64_t m_hist_cap, int P) {
+  s.ng1 = cv.take<int32_t>(m_hist_cap);
+  s.gs1 = cv.take<int32_t>(m_hist_cap * (P + 1));
+  s.ng2 = cv.take<int32_t>(m_hist_cap);
+  s.gs2 = cv.take<int32_t>(m_hist_cap * (P + 1));
+  s.item_off1 = cv.take<int64_t>(m_hist_cap + 1);
+  s.item_off2 = cv.take<int64_t>(m_hist_cap + 1);
+  s.item_total = cv.take<V4>(1);
+  s.tiles = cv.take<V4>(scan_tiles_for(m_hist_cap) + 1);
+}
+
+template <int KMAX>
+cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes, int64_t m_hist_cap,
+                            const StagedScratch& ss, uint32_t* mm, int32_t* hist, int64_t S, cudaStream_t st) {
+  const DeviceInfo& di = device_info();
+  const int P = a.pv.P, C = a.ds.C, B = a.B, d = a.ds.d;
+  const int PG = hist_group_size(B, C);
+  cudaError_t e;
+  {
+    const size_t smem = (size_t)4 * (((d + 31) >> 5) + kStUMax) * 4;
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    ProfScope ps_("k_groups", st);
+    k_groups<<<di.num_sms * 2, 128, smem, st>>>(plan_total, hist_nodes, a.pv, d, kStUMax, kMmGroup, kStUMax, PG,
+                                                ss.ng1, ss.gs1, ss.ng2, ss.gs2);
+  }
+  ItemScanF isf{plan_total, hist_nodes, a.node_off, ss.ng1, ss.ng2, S, ss.item_off1, ss.item_off2};
+  e = run_scan(isf, m_hist_cap, ss.tiles, ss.item_total, st, "item_scan");
+  if (e != cudaSuccess) return e;
+  StagedPlan sp1{plan_total, hist_nodes, a.node_off, ss.ng1, ss.gs1, ss.item_off1, ss.item_total, 0, S};
+  StagedPlan sp2{plan_total, hist_nodes, a.node_off, ss.ng2, ss.gs2, ss.item_off2, ss.item_total, 1, S};
+  {
+    const size_t smem = mm_smem_bytes(d, KMAX);
+    e = cudaFuncSetAttribute(k_mm_staged<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mm_staged<KMAX>, kStThreads, smem);
+    if (occ < 1) occ = 1;
+    ProfScope ps_("k_minmax", st);
+    k_mm_staged<KMAX><<<di.num_sms * occ, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp1, mm);
+  }
+  {
+    const size_t smem = hist_smem_bytes(d, KMAX, B, C, PG);
+    e = cudaFuncSetAttribute(k_hist_staged<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ProfScope ps_("k_hist", st);
+    k_hist_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp2, B, PG, mm, hist);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_staged(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes, int64_t m_hist_cap,
+                          const StagedScratch& ss, uint32_t* mm, int32_t* hist, int64_t S, int kmax,
+                          cudaStream_t st) {
+  if (kmax <= 8) return launch_staged_k<8>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, S, st);
+  if (kmax <= 16) return launch_staged_k<16>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, S, st);
+  return launch_staged_k<32>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, S, st);
+}
+
+}  // namespace sof

@@ -77,6 +77,7 @@ struct SearchArgs {
   int32_t T = 1024;
   int32_t hist_only = 0;
   float eps = 4e-6f;
+  int32_t max_nnz = kMaxCap;        // upper bound of projection row lengths
   so_split* out = nullptr;          // device [m]
   int64_t* left_counts = nullptr;   // device [m*C] or null
   // inspection outputs (so_histograms): all nodes forced onto the histogram path
@@ -84,6 +85,18 @@ struct SearchArgs {
   int32_t* hist_out = nullptr;
   float* gain32_out = nullptr;
   HistTuning tune{};
+};
+
+// Scratch of the staged-tile histogram kernels (so_hist_staged.cu).
+struct StagedScratch {
+  int32_t* ng1 = nullptr;      // groups per histogram node (min/max kernel)
+  int32_t* gs1 = nullptr;      // [m_hist_cap][P+1] group starts
+  int32_t* ng2 = nullptr;      // groups per histogram node (histogram kernel)
+  int32_t* gs2 = nullptr;
+  int64_t* item_off1 = nullptr;
+  int64_t* item_off2 = nullptr;
+  V4* item_total = nullptr;
+  V4* tiles = nullptr;
 };
 
 // Device scratch of one search (carved from a workspace).
@@ -97,8 +110,9 @@ struct SearchScratch {
   float* max32 = nullptr;       // [m_hist_cap*P]
   int32_t* node_counts = nullptr;  // [m_hist_cap*C]
   int32_t* hist = nullptr;      // [m_hist_cap*P*B*C]
-  int32_t* err = nullptr;       // [1]
+  int32_t* err = nullptr;       // [m+1] per-node bad-input flags
   int64_t m_hist_cap = 0;
+  StagedScratch staged;
 };
 
 // Carves a SearchScratch (dry run gives the size).
@@ -127,6 +141,13 @@ struct DeviceInfo {
 const DeviceInfo& device_info();
 
 cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStream_t st);
+
+// staged-tile histogram path (features up to 65536)
+bool staged_supported(int d);
+void carve_staged(Carver& cv, StagedScratch& s, int64_t m_hist_cap, int P);
+cudaError_t launch_staged(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes,
+                          int64_t m_hist_cap, const StagedScratch& ss, uint32_t* mm, int32_t* hist,
+                          int64_t S, int kmax, cudaStream_t st);
 
 // ---- partition ------------------------------------------------------------
 // Per-node instruction for the batched stable partition.

@@ -53,11 +53,11 @@ const DeviceInfo& device_info() {
 // Rows must hold 1..32 distinct ascending features in [0, d) with +-1 signs.
 // A node with a bad row is marked and skipped (path -2); kernels additionally
 // clamp what they load so that a bad row can never address outside X.
-__global__ void k_validate_rows(ProjView pv, int32_t m, int32_t d, int32_t* bad_node) {
+__global__ void k_validate_rows(ProjView pv, int32_t m, int32_t d, int32_t max_nnz, int32_t* bad_node) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)m * pv.P) return;
   const int32_t b = pv.beg[q], e = pv.end[q];
-  bool ok = (e - b >= 1) && (e - b <= kMaxCap) && b >= 0;
+  bool ok = (e - b >= 1) && (e - b <= max_nnz) && b >= 0;
   if (ok) {
     int prev = -1;
     for (int i = b; i < e; ++i) {
@@ -865,6 +865,7 @@ void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int3
   s.max32 = cv.take<float>((size_t)mh * P);
   s.node_counts = cv.take<int32_t>((size_t)mh * C);
   s.hist = cv.take<int32_t>((size_t)mh * P * B * C);
+  carve_staged(cv, s.staged, mh, P);
 }
 
 namespace {
@@ -890,7 +891,7 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
   if (e != cudaSuccess) return e;
   {
     const int64_t rows = (int64_t)a.m * P;
-    if (rows > 0) k_validate_rows<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a.pv, a.m, a.ds.d, s.err);
+    if (rows > 0) k_validate_rows<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a.pv, a.m, a.ds.d, a.max_nnz, s.err);
   }
   PlanF pf;
   pf.off = a.node_off;
@@ -916,24 +917,25 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
     ProfScope ps_("k_hist_init", st);
     k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
   }
-  {
-    static thread_local int occ_mm = 0;
-    if (!occ_mm) occ_mm = occupancy(k_minmax<PG>, PG * 32, 0);
+  if (staged_supported(a.ds.d)) {
+    e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, S, a.max_nnz, st);
+    if (e != cudaSuccess) return e;
+  } else {
     {
+      static thread_local int occ_mm = 0;
+      if (!occ_mm) occ_mm = occupancy(k_minmax<PG>, PG * 32, 0);
       ProfScope ps_("k_minmax", st);
       k_minmax<PG><<<di.num_sms * occ_mm, PG * 32, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
                                                             s.hist_nodes, s.item_off, S, s.mm_keys);
     }
-  }
-  {
-    const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
-    e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int occ = occupancy(k_hist<PG>, PG * 32, smem);
     {
+      const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
+      e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const int occ = occupancy(k_hist<PG>, PG * 32, smem);
       ProfScope ps_("k_hist", st);
-      k_hist<PG><<<di.num_sms * occ, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.hist_nodes,
-                                                          s.item_off, S, B, s.mm_keys, s.hist);
+      k_hist<PG><<<di.num_sms * occ, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
+                                                          s.hist_nodes, s.item_off, S, B, s.mm_keys, s.hist);
     }
   }
   {
@@ -985,7 +987,7 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
   cudaError_t e = cudaMemsetAsync(s.err, 0, sizeof(int32_t) * ((size_t)a.m + 1), st);
   if (e != cudaSuccess) return e;
   const int64_t rows = (int64_t)a.m * P;
-  if (rows > 0) k_validate_rows<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a.pv, a.m, a.ds.d, s.err);
+  if (rows > 0) k_validate_rows<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a.pv, a.m, a.ds.d, a.max_nnz, s.err);
   PlanF pf;
   pf.off = a.node_off;
   pf.n_total = a.n_total;
@@ -1009,18 +1011,23 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
     ProfScope ps_("k_hist_init", st);
     k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
   }
-  {
-    ProfScope ps_("k_minmax", st);
-    k_minmax<PG><<<di.num_sms * 4, PG * 32, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.hist_nodes,
-                                                     s.item_off, S, s.mm_keys);
-  }
-  const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
-  e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  {
-    ProfScope ps_("k_hist", st);
-    k_hist<PG><<<di.num_sms * 2, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.hist_nodes,
-                                                      s.item_off, S, B, s.mm_keys, s.hist);
+  if (staged_supported(a.ds.d)) {
+    e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, S, a.max_nnz, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    {
+      ProfScope ps_("k_minmax", st);
+      k_minmax<PG><<<di.num_sms * 4, PG * 32, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.hist_nodes,
+                                                       s.item_off, S, s.mm_keys);
+    }
+    const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
+    e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    {
+      ProfScope ps_("k_hist", st);
+      k_hist<PG><<<di.num_sms * 2, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.hist_nodes,
+                                                        s.item_off, S, B, s.mm_keys, s.hist);
+    }
   }
   {
     ProfScope ps_("k_gini_scan", st);

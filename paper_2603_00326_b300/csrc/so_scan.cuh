@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, int64_t n, V4
 }
 
 // One block: exclusive scan of the tile sums in place; total to *total.
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(V4* tiles, int64_t n_tiles, V4* total) {
+static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(V4* tiles, int64_t n_tiles, V4* total) {
   __shared__ V4 tot;
   V4 carry = v4zero();
   for (int64_t base = 0; base < n_tiles; base += kScanThreads) {

@@ -32,7 +32,8 @@ class so_dataset(C.Structure):
 
 
 class so_projs(C.Structure):
-    _fields_ = [("n_proj", C.c_int32), ("ptr", C.c_void_p), ("feat", C.c_void_p), ("sign", C.c_void_p)]
+    _fields_ = [("n_proj", C.c_int32), ("ptr", C.c_void_p), ("feat", C.c_void_p), ("sign", C.c_void_p),
+                ("max_nnz", C.c_int32)]
 
 
 class so_split_params(C.Structure):
@@ -152,14 +153,17 @@ class DeviceDataset:
 
 @dataclasses.dataclass
 class DeviceProjs:
-    """CSR projection rows on the device: ptr int32 [rows+1], feat int32, sign int8."""
+    """CSR projection rows on the device: ptr int32 [rows+1], feat int32, sign int8.
+    max_nnz: upper bound of the row lengths (0 = unknown)."""
     n_proj: int
     ptr: "object"
     feat: "object"
     sign: "object"
+    max_nnz: int = 0
 
     def c(self) -> so_projs:
-        return so_projs(self.n_proj, self.ptr.data_ptr(), self.feat.data_ptr(), self.sign.data_ptr())
+        return so_projs(self.n_proj, self.ptr.data_ptr(), self.feat.data_ptr(), self.sign.data_ptr(),
+                        self.max_nnz)
 
 
 def split_params(n_bins=256, sort_below=1024, hist_only=False, rescore_rel_eps=0.0) -> so_split_params:

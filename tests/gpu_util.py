@@ -19,12 +19,16 @@ def upload_dataset(X, y, C):
     return S.DeviceDataset(Xt, yt, C)
 
 
-def upload_projs(ptr, feat, sign, P):
+def upload_projs(ptr, feat, sign, P, max_nnz=None):
+    """max_nnz=None: the true longest row (selects the narrowest kernel variant);
+    0: unknown (widest variant)."""
     torch = torch_cuda()
     from paper_2603_00326_b300 import soforest as S
+    if max_nnz is None:
+        max_nnz = int(np.diff(np.asarray(ptr)).max()) if len(ptr) > 1 else 0
     return S.DeviceProjs(P, torch.from_numpy(np.ascontiguousarray(ptr, np.int32)).cuda(),
                          torch.from_numpy(np.ascontiguousarray(feat, np.int32)).cuda(),
-                         torch.from_numpy(np.ascontiguousarray(sign, np.int8)).cuda())
+                         torch.from_numpy(np.ascontiguousarray(sign, np.int8)).cuda(), max_nnz)
 
 
 def i32(a):

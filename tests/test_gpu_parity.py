@@ -76,7 +76,7 @@ def test_histogram_stage_parity(S, B, C):
                 np.concatenate([[5], f0[k0:]]).astype(np.int32), np.concatenate([[1], s0[k0:]]).astype(np.int8))
     ptr, feat, sign = U.concat_projs(projs)
     ds = U.upload_dataset(X, y, C)
-    pj = U.upload_projs(ptr, feat, sign, P)
+    pj = U.upload_projs(ptr, feat, sign, P, max_nnz=None if B != 64 else 0)
     mm, hist, g32 = S.so_histograms(ds, U.i32(idx), U.i64(off), pj, B, want_gains=True)
     mm, hist, g32 = mm.cpu().numpy(), hist.cpu().numpy(), g32.cpu().numpy()
     worst = 0.0
@@ -95,6 +95,59 @@ def test_histogram_stage_parity(S, B, C):
             if rel.size:
                 worst = max(worst, float(rel.max()))
     assert worst <= GAIN32_REL_TOL, worst
+
+
+@pytest.mark.parametrize("d,cap,P", [(4096, 16, 96), (600, 32, 40), (70000, 8, 8)])
+def test_histogram_stage_wide(S, d, cap, P):
+    """Wide data: projection groups are formed on the device under the tile's
+    feature budget; groups wider than a tile take the direct path; more than
+    65536 features use the general kernels."""
+    rng = np.random.default_rng(d + cap)
+    n = 3000 if d > 10000 else 20000
+    X = rng.standard_normal((d, n)).astype(np.float32)
+    y = rng.integers(0, 3, n).astype(np.uint8)
+    sizes = [4000, 2500, 333] if n > 5000 else [2000, 999]
+    idx, off = _mixed_nodes(rng, n, sizes)
+    projs = [G.random_projections(rng, P, d, 8.0, cap) for _ in sizes]
+    ptr, feat, sign = U.concat_projs([(p.ptr, p.feat, p.sign) for p in projs])
+    ds = U.upload_dataset(X, y, 3)
+    pj = U.upload_projs(ptr, feat, sign, P)
+    mm, hist, _ = S.so_histograms(ds, U.i32(idx), U.i64(off), pj, 256)
+    mm, hist = mm.cpu().numpy(), hist.cpu().numpy()
+    for j in range(len(sizes)):
+        nptr, nf, ns = U.oracle_node_projs(ptr, feat, sign, P, j)
+        r = O.split_search(X, y, 3, idx[off[j]:off[j + 1]], nptr, nf, ns, hist_only=True, want_debug=True)
+        np.testing.assert_array_equal(U.f32bits(mm[j]), U.f32bits(r.minmax), err_msg=f"minmax node {j}")
+        np.testing.assert_array_equal(hist[j], r.hist, err_msg=f"hist node {j}")
+
+
+def test_ill_conditioned_ranges(S):
+    """Projections whose range is tiny against their magnitude (a few ulps wide
+    up to 2^-20 of the value) take the exact bin rule; boundaries coincide."""
+    rng = np.random.default_rng(77)
+    n, d = 5000, 6
+    base = np.float32(1000.0)
+    X = np.empty((d, n), np.float32)
+    X[0] = base + np.float32(2.0 ** -13) * rng.integers(0, 4, n).astype(np.float32)   # 4 distinct values
+    X[1] = np.where(rng.random(n) < 0.5, base, np.nextafter(base, np.float32(2000)))
+    X[2] = rng.standard_normal(n).astype(np.float32) * np.float32(1e-3) + np.float32(7.0)
+    X[3] = rng.standard_normal(n).astype(np.float32)
+    X[4] = np.float32(3.0)
+    X[5] = rng.standard_normal(n).astype(np.float32) * np.float32(1e4)
+    y = rng.integers(0, 2, n).astype(np.uint8)
+    ptr = np.arange(d + 1, dtype=np.int32)
+    feat = np.arange(d, dtype=np.int32)
+    sign = np.ones(d, np.int8)
+    idx = np.arange(n, dtype=np.int32)
+    off = np.array([0, n], np.int64)
+    ds = U.upload_dataset(X, y, 2)
+    pj = U.upload_projs(ptr, feat, sign, d)
+    mm, hist, _ = S.so_histograms(ds, U.i32(idx), U.i64(off), pj, 256)
+    r = O.split_search(X, y, 2, idx, ptr, feat, sign, hist_only=True, want_debug=True)
+    np.testing.assert_array_equal(U.f32bits(mm.cpu().numpy()[0]), U.f32bits(r.minmax))
+    np.testing.assert_array_equal(hist.cpu().numpy()[0], r.hist)
+    out, _ = S.so_split_search(ds, U.i32(idx), pj, S.split_params(256, 0, True))
+    U.assert_split_equal(out, r)
 
 
 # ---------------------------------------------------------------- single-node search
@@ -123,7 +176,7 @@ def test_split_search_single_parity(S, case, C):
     idx = rng.integers(0, n_data, case["n"]).astype(np.int32)
     pr = G.random_projections(rng, P, d, 1.5, 8)
     ds = U.upload_dataset(X, y, C)
-    pj = U.upload_projs(pr.ptr, pr.feat, pr.sign, P)
+    pj = U.upload_projs(pr.ptr, pr.feat, pr.sign, P, max_nnz=None if C == 2 else 0)
     prm = S.split_params(256, case["T"], case["hist_only"])
     out, lc = S.so_split_search(ds, U.i32(idx), pj, prm)
     r = O.split_search(X, y, C, idx, pr.ptr, pr.feat, pr.sign, sort_below=case["T"], hist_only=case["hist_only"])
