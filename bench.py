@@ -126,6 +126,87 @@ def cpu_baseline(ds, pr, n_sample_proj: int):
     return ds.n * n_sample_proj / dt, dt
 
 
+def extra_legs(S, torch, dev):
+    """Secondary measurements: the batched frontier against the node-at-a-time
+    form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
+    64 projections/node, T=1024), and one tree grown to purity (tree_small)."""
+    from paper_2603_00326_b300 import datagen as G
+    out = {}
+    ds_np = G.frontier_1m()
+    p = G.WORKLOAD_PARAMS["frontier_1m"]
+    idx_np, off_np = G.frontier_nodes(ds_np.n, p["n_nodes"])
+    rng = np.random.default_rng(G.PROJ_SEED_BASE + 2)
+    m, P = p["n_nodes"], p["n_proj"]
+    projs = [G.random_projections(rng, P, ds_np.d, p["lam"], p["cap"]) for _ in range(m)]
+    ptrs = [np.zeros(1, np.int32)]
+    base = 0
+    for q in projs:
+        ptrs.append(q.ptr[1:] + base)
+        base += int(q.ptr[-1])
+    ptr = np.concatenate(ptrs).astype(np.int32)
+    feat = np.concatenate([q.feat for q in projs]).astype(np.int32)
+    sign = np.concatenate([q.sign for q in projs]).astype(np.int8)
+    dd = S.DeviceDataset(torch.from_numpy(ds_np.X).to(dev), torch.from_numpy(ds_np.y).to(dev), 2)
+    cap = int(p["cap"])
+    pj = S.DeviceProjs(P, torch.from_numpy(ptr).to(dev), torch.from_numpy(feat).to(dev),
+                       torch.from_numpy(sign).to(dev), cap)
+    idx = torch.from_numpy(idx_np).to(dev)
+    off = torch.from_numpy(off_np).to(dev)
+    prm = S.split_params(256, p["sort_below"], False)
+    ws = torch.empty(S.so_split_search_ws_bytes(m, ds_np.n, P, 2, prm), dtype=torch.uint8, device=dev)
+    outb = torch.empty(m * S.SPLIT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        S.so_split_search_batch(dd, idx, off, pj, prm, out=outb, workspace=ws)
+    torch.cuda.synchronize()
+    reps = 10
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        S.so_split_search_batch(dd, idx, off, pj, prm, out=outb, workspace=ws)
+    torch.cuda.synchronize()
+    batched_ms = (time.perf_counter() - t0) * 1000.0 / reps
+    # node-at-a-time: one synchronous call per node (the paper's offload form)
+    views = []
+    for j in range(m):
+        a, b = int(off_np[j]), int(off_np[j + 1])
+        r0, r1 = int(ptr[j * P]), int(ptr[(j + 1) * P])
+        views.append((idx[a:b], S.DeviceProjs(P, pj.ptr[j * P:(j + 1) * P + 1] - r0, pj.feat[r0:r1],
+                                              pj.sign[r0:r1], cap)))
+    wsn = torch.empty(S.so_split_search_ws_bytes(1, int(np.diff(off_np).max()), P, 2, prm) + 4096 + 1024,
+                      dtype=torch.uint8, device=dev)
+    for j in range(min(m, 64)):
+        S.so_split_search(dd, views[j][0], views[j][1], prm, workspace=wsn)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for j in range(m):
+        plain.append(S.so_split_search(dd, views[j][0], views[j][1], prm, workspace=wsn)[0])
+    plain_ms = (time.perf_counter() - t0) * 1000.0
+    rec = S.splits_to_numpy(outb)
+    same = all(int(rec[j]["proj"]) == plain[j].proj and int(rec[j]["cand"]) == plain[j].cand and
+               float(rec[j]["gain"]) == plain[j].gain for j in range(m))
+    sp = float(ds_np.n * P)
+    out["frontier_1m"] = {"nodes": m, "batched_ms": batched_ms, "plain_ms": plain_ms,
+                          "speedup": plain_ms / batched_ms, "identical": bool(same),
+                          "batched_sample_projections_per_s": sp / (batched_ms / 1000.0)}
+    del dd, idx, off, ws, outb, views
+    # one tree to purity
+    ts = G.tree_small()
+    tp = G.WORKLOAD_PARAMS["tree_small"]
+    dd = S.DeviceDataset(torch.from_numpy(ts.X).to(dev), torch.from_numpy(ts.y).to(dev), 2)
+    root = torch.from_numpy(G.all_indices(ts.n)).to(dev)
+    prm = S.tree_params(tp["n_proj"], tp["lam"], tp["cap"], 256, tp["sort_below"], seed=G.PROJ_SEED_BASE)
+    S.so_train_tree(dd, root, prm)
+    times = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr = S.so_train_tree(dd, root, prm)
+        times.append(time.perf_counter() - t0)
+    out["tree_small"] = {"train_s": min(times), "median_s": statistics.median(times), "nodes": tr.n_nodes,
+                         "depth": int(tr.depth.max())}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -283,6 +364,8 @@ def run_ours(args):
         "split": {"proj": int(rec["proj"]), "cand": int(rec["cand"]), "gain": float(rec["gain"]),
                   "n_left": int(rec["n_left"])},
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["extras"] = extra_legs(S, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt = cpu_baseline(ds_np, pr, 32)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -304,6 +387,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
+    ap.add_argument("--no-extras", action="store_true", help="skip the frontier and tree legs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -450,10 +450,11 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   const int nw = (ds.d + 31) >> 5;
   const int C = ds.C;
   const int HS = (B + 1) * C;  // words per projection histogram
+  // every region starts on a 16-byte boundary (s_y4 is read as int2)
   float* s_tile = reinterpret_cast<float*>(s_raw);                        // [kStThreads*kStEpt]
-  int32_t* s_hist = reinterpret_cast<int32_t*>(s_tile + kStThreads * kStEpt);  // [(PG+1)*HS]
-  int* s_y4 = s_hist + (PG + 1) * HS;                                     // [256] byte offset of the label
-  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_y4 + 256);             // [nw]
+  int* s_y4 = reinterpret_cast<int*>(s_tile + kStThreads * kStEpt);       // [256] byte offset of the label
+  int32_t* s_hist = s_y4 + 256;                                           // [(PG+1)*HS]
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_hist + (((PG + 1) * HS + 3) & ~3));  // [nw]
   int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                      // [nw]
   int* s_rowfeat = s_wpre + nw;                                           // [kStUMax]
   int* s_dk = s_rowfeat + kStUMax;                                        // [PG]
@@ -599,8 +600,9 @@ size_t mm_smem_bytes(int d, int kmax) {
 }
 size_t hist_smem_bytes(int d, int kmax, int B, int C, int PG) {
   const int nw = (d + 31) >> 5;
-  return (size_t)kStThreads * kStEpt * 4 + (size_t)(PG + 1) * (B + 1) * C * 4 + 256 * 4 + (size_t)nw * 8 +
-         kStUMax * 4 + 32 * 4 + (size_t)32 * kmax * 6 + 64;
+  const size_t hist_words = ((size_t)(PG + 1) * (B + 1) * C + 3) & ~(size_t)3;
+  return (size_t)kStThreads * kStEpt * 4 + 256 * 4 + hist_words * 4 + (size_t)nw * 8 + kStUMax * 4 + 32 * 4 +
+         (size_t)32 * kmax * 6 + 64;
 }
 
 bool staged_supported(int d) { return d <= kStMaxWords * 32; }
