@@ -41,26 +41,25 @@ constexpr float kMagic = 12582912.0f;    // 1.5 * 2^23
 constexpr float kCondLimit = 262144.0f;  // 2^18
 
 // ---- packed FP32x2 (sm_100+ PTX) ------------------------------------------
-__device__ __forceinline__ unsigned long long as_u64(float2 a) {
-  return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
-}
-__device__ __forceinline__ float2 as_f2(unsigned long long u) {
-  return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
-}
+// Pairs are formed and split with mov.b64 so they stay register pairs.
+// fadd2 results are only used where a later fusion could not change them.
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)), "l"(as_u64(c)));
-  return as_f2(d);
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
 }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)));
-  return as_f2(d);
-}
-__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)));
-  return as_f2(d);
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 
 // ---- staged plan ------------------------------------------------------------
@@ -193,36 +192,85 @@ __device__ __forceinline__ void build_desc(const ProjView& pv, int64_t qbase, in
 }
 
 // ---- tile staging through registers (prefetch of the next tile) -------------
-// Thread owns tile column i = tid % St and rows tid/St + k*(NT/St).
+// Scalar form: thread owns tile column i = tid % St and rows tid/St + k*(NT/St),
+// one gather per element.  Vector form (a full tile of consecutive, 16-byte
+// aligned samples): thread owns float4 column tid % (St/4).  Threads tid < St
+// also fetch the label of tile position tid.
 struct TileLoader {
   float pre[kStEpt];
-  int sid;
-  bool valid;
+  int ylab;  // label of position tid (tid < St), -1 for padding
   __device__ __forceinline__ void load(const DatasetView& ds, const int32_t* __restrict__ idx, int64_t tbeg,
-                                       int64_t tend, int St, int U, const int* s_rowfeat) {
-    const int i = threadIdx.x % St;
-    const int r0 = threadIdx.x / St;
-    const int rstep = kStThreads / St;
-    const int64_t pos = tbeg + i;
-    valid = pos < tend;
-    sid = (int)safe_sample(idx[valid ? pos : tbeg], ds.n);
+                                       int64_t tend, int St, int U, const int* s_rowfeat, bool vec) {
+    if (vec) {
+      const int nq = St >> 2;
+      const int q = threadIdx.x & (nq - 1);
+      const int r0 = threadIdx.x / nq;
+      const int rstep = kStThreads / nq;
+      const int64_t sid0 = idx[tbeg];
 #pragma unroll
-    for (int k = 0; k < kStEpt; ++k) {
-      const int r = r0 + k * rstep;
-      if (r < U) pre[k] = __ldg(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid);
+      for (int k = 0; k < kStEpt / 4; ++k) {
+        const int r = r0 + k * rstep;
+        if (r < U) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid0) + q);
+          pre[4 * k] = v.x;
+          pre[4 * k + 1] = v.y;
+          pre[4 * k + 2] = v.z;
+          pre[4 * k + 3] = v.w;
+        }
+      }
+      if (threadIdx.x < St) ylab = ds.y[sid0 + threadIdx.x];
+    } else {
+      const int i = threadIdx.x % St;
+      const int r0 = threadIdx.x / St;
+      const int rstep = kStThreads / St;
+      const int64_t pos = tbeg + i;
+      const bool valid = pos < tend;
+      // padding positions repeat the tile's first sample (min / max unchanged)
+      const int64_t sid = safe_sample(idx[valid ? pos : tbeg], ds.n);
+#pragma unroll
+      for (int k = 0; k < kStEpt; ++k) {
+        const int r = r0 + k * rstep;
+        if (r < U) pre[k] = __ldg(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid);
+      }
+      if (threadIdx.x < St) ylab = valid ? (int)ds.y[sid] : -1;
     }
   }
-  __device__ __forceinline__ void store(float* s_tile, int St, int U) const {
-    const int i = threadIdx.x % St;
-    const int r0 = threadIdx.x / St;
-    const int rstep = kStThreads / St;
+  __device__ __forceinline__ void store(float* s_tile, int St, int U, bool vec) const {
+    if (vec) {
+      const int nq = St >> 2;
+      const int q = threadIdx.x & (nq - 1);
+      const int r0 = threadIdx.x / nq;
+      const int rstep = kStThreads / nq;
 #pragma unroll
-    for (int k = 0; k < kStEpt; ++k) {
-      const int r = r0 + k * rstep;
-      if (r < U) s_tile[r * St + i] = pre[k];
+      for (int k = 0; k < kStEpt / 4; ++k) {
+        const int r = r0 + k * rstep;
+        if (r < U)
+          reinterpret_cast<float4*>(s_tile + r * St)[q] =
+              make_float4(pre[4 * k], pre[4 * k + 1], pre[4 * k + 2], pre[4 * k + 3]);
+      }
+    } else {
+      const int i = threadIdx.x % St;
+      const int r0 = threadIdx.x / St;
+      const int rstep = kStThreads / St;
+#pragma unroll
+      for (int k = 0; k < kStEpt; ++k) {
+        const int r = r0 + k * rstep;
+        if (r < U) s_tile[r * St + i] = pre[k];
+      }
     }
   }
 };
+
+// Whether the item's samples are one run of consecutive indices that the
+// vector form may read directly (all threads call; one barrier).
+__device__ __forceinline__ bool item_contiguous(const DatasetView& ds, const int32_t* __restrict__ idx, int64_t beg,
+                                                int64_t end) {
+  const int64_t first = idx[beg];
+  bool ok = first >= 0 && first + (end - beg) <= ds.n && (first & 3) == 0 && (ds.ld & 3) == 0 &&
+            ((reinterpret_cast<uintptr_t>(ds.X) & 15) == 0);
+  for (int64_t e = beg + threadIdx.x; ok && e < end; e += kStThreads) ok = (idx[e] == first + (e - beg));
+  return __syncthreads_and(ok) != 0;
+}
 
 __device__ __forceinline__ int choose_st(int U) {
   // U * St <= kStThreads * kStEpt, St in {64, 128, 256}
@@ -329,13 +377,58 @@ struct ItemScanF {
 };
 
 // ---- k_mm_staged: min / max -------------------------------------------------
+// Per (projection, tile): the warp of the projection evaluates every sample
+// pair of the tile with the projection's rows and signs in registers (the
+// loop is specialised on the projection's non-zero count K); per-lane running
+// minima and maxima live in shared memory until the item ends.
+template <int K>
+__device__ __forceinline__ void mm_tile(const float* __restrict__ s_tile, const int16_t* drow, const float* dsg,
+                                        int St, int lane, float& mn, float& mx) {
+  int roff[K];
+  float2 sg[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    roff[j] = drow[j] * St + 2 * lane;
+    sg[j] = make_float2(dsg[j], dsg[j]);
+  }
+  for (int ps = 0; ps < St; ps += 64) {
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
+    mn = fminf(mn, fminf(acc.x, acc.y));
+    mx = fmaxf(mx, fmaxf(acc.x, acc.y));
+  }
+}
+
+template <int KMAX>
+__device__ __forceinline__ void mm_tile_k(int k, const float* s_tile, const int16_t* drow, const float* dsg, int St,
+                                          int lane, float& mn, float& mx) {
+  switch (k) {
+#define SOF_MM_CASE(N) \
+  case N:              \
+    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1)>(s_tile, drow, dsg, St, lane, mn, mx); \
+    break;
+    SOF_MM_CASE(1) SOF_MM_CASE(2) SOF_MM_CASE(3) SOF_MM_CASE(4) SOF_MM_CASE(5) SOF_MM_CASE(6) SOF_MM_CASE(7)
+    SOF_MM_CASE(8) SOF_MM_CASE(9) SOF_MM_CASE(10) SOF_MM_CASE(11) SOF_MM_CASE(12) SOF_MM_CASE(13)
+    SOF_MM_CASE(14) SOF_MM_CASE(15) SOF_MM_CASE(16) SOF_MM_CASE(17) SOF_MM_CASE(18) SOF_MM_CASE(19)
+    SOF_MM_CASE(20) SOF_MM_CASE(21) SOF_MM_CASE(22) SOF_MM_CASE(23) SOF_MM_CASE(24) SOF_MM_CASE(25)
+    SOF_MM_CASE(26) SOF_MM_CASE(27) SOF_MM_CASE(28) SOF_MM_CASE(29) SOF_MM_CASE(30) SOF_MM_CASE(31)
+    SOF_MM_CASE(32)
+#undef SOF_MM_CASE
+    default:
+      break;
+  }
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, const int32_t* __restrict__ idx,
                                                             ProjView pv, StagedPlan sp, uint32_t* mm) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
   float* s_tile = reinterpret_cast<float*>(s_raw);                       // [kStThreads*kStEpt]
-  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_tile + kStThreads * kStEpt);  // [nw]
+  float* s_pmin = s_tile + kStThreads * kStEpt;                          // [kMmGroup*32]
+  float* s_pmax = s_pmin + kMmGroup * 32;                                // [kMmGroup*32]
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_pmax + kMmGroup * 32);  // [nw]
   int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                     // [nw]
   int* s_rowfeat = s_wpre + nw;                                          // [kStUMax]
   int* s_dk = s_rowfeat + kStUMax;                                       // [kMmGroup]
@@ -351,60 +444,42 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
     __syncthreads();  // previous item done with shared memory
     const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
     build_desc<KMAX>(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_dk, s_drow, s_dsg);
-    __syncthreads();
-    float mn[kMmPPW], mx[kMmPPW];
-#pragma unroll
-    for (int i = 0; i < kMmPPW; ++i) {
-      mn[i] = INFINITY;
-      mx[i] = -INFINITY;
+    for (int e = threadIdx.x; e < it.np * 32; e += kStThreads) {
+      s_pmin[e] = INFINITY;
+      s_pmax[e] = -INFINITY;
     }
+    const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
     if (U <= kStUMax) {
       const int St = choose_st(U);
       const int64_t len = it.end - it.beg;
       const int64_t ntile = (len + St - 1) / St;
       TileLoader ld;
-      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat);
+      bool vec = contig && len >= St;
+      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat, vec);
       for (int64_t tt = 0; tt < ntile; ++tt) {
         __syncthreads();
-        ld.store(s_tile, St, U);
+        ld.store(s_tile, St, U, vec);
         __syncthreads();
         if (tt + 1 < ntile) {
           const int64_t nb = it.beg + (tt + 1) * St;
-          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat);
+          vec = contig && (it.end - nb) >= St;
+          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat, vec);
         }
-        // positions beyond the chunk repeat the tile's first sample, so they
-        // never change a minimum or maximum
-#pragma unroll
-        for (int i = 0; i < kMmPPW; ++i) {
-          const int pl = warp * kMmPPW + i;
-          if (pl < it.np) {
-            const int k = s_dk[pl];
-            for (int ps = 0; ps < St; ps += 64) {
-              const int i0 = ps + 2 * lane;
-              float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-              for (int jj = 0; jj < KMAX; ++jj) {
-                if (jj < k) {
-                  const float2 x = *reinterpret_cast<const float2*>(s_tile + s_drow[pl * KMAX + jj] * St + i0);
-                  const float s = s_dsg[pl * KMAX + jj];
-                  acc = ffma2(make_float2(s, s), x, acc);
-                }
-              }
-              mn[i] = fminf(mn[i], fminf(acc.x, acc.y));
-              mx[i] = fmaxf(mx[i], fmaxf(acc.x, acc.y));
-            }
-          }
+        for (int pl = warp; pl < it.np; pl += kStWarps) {
+          float mn = s_pmin[pl * 32 + lane], mx = s_pmax[pl * 32 + lane];
+          mm_tile_k<KMAX>(s_dk[pl], s_tile, s_drow + pl * KMAX, s_dsg + pl * KMAX, St, lane, mn, mx);
+          s_pmin[pl * 32 + lane] = mn;
+          s_pmax[pl * 32 + lane] = mx;
         }
       }
     } else {
       // direct path for wide groups: each warp gathers its projections' features
-      for (int i = 0; i < kMmPPW; ++i) {
-        const int pl = warp * kMmPPW + i;
-        if (pl >= it.np) break;
+      for (int pl = warp; pl < it.np; pl += kStWarps) {
         const int64_t q = qbase + pl;
         const int rb = pv.beg[q];
         int k = pv.end[q] - rb;
         k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
+        float mn = INFINITY, mx = -INFINITY;
         for (int64_t e = it.beg + lane; e < it.end; e += 32) {
           const int64_t s = safe_sample(idx[e], ds.n);
           float acc = 0.0f;
@@ -414,24 +489,17 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
             const float x = __ldg(ds.X + (int64_t)f * ds.ld + s);
             acc = __fadd_rn(acc, pv.sign[rb + jj] == 1 ? x : -x);
           }
-          mn[0] = fminf(mn[0], acc);
-          mx[0] = fmaxf(mx[0], acc);
+          mn = fminf(mn, acc);
+          mx = fmaxf(mx, acc);
         }
-        const float a = warp_min(mn[0]), b = warp_max(mx[0]);
-        if (lane == 0) {
-          atomicMin(&mm[(it.h * P + it.p0 + pl) * 2], f2key(a));
-          atomicMax(&mm[(it.h * P + it.p0 + pl) * 2 + 1], f2key(b));
-        }
-        mn[0] = INFINITY;
-        mx[0] = -INFINITY;
+        s_pmin[pl * 32 + lane] = mn;
+        s_pmax[pl * 32 + lane] = mx;
       }
-      continue;
     }
-#pragma unroll
-    for (int i = 0; i < kMmPPW; ++i) {
-      const int pl = warp * kMmPPW + i;
-      const float a = warp_min(mn[i]), b = warp_max(mx[i]);
-      if (lane == 0 && pl < it.np) {
+    __syncthreads();
+    for (int pl = warp; pl < it.np; pl += kStWarps) {
+      const float a = warp_min(s_pmin[pl * 32 + lane]), b = warp_max(s_pmax[pl * 32 + lane]);
+      if (lane == 0) {
         atomicMin(&mm[(it.h * P + it.p0 + pl) * 2], f2key(a));
         atomicMax(&mm[(it.h * P + it.p0 + pl) * 2 + 1], f2key(b));
       }
@@ -441,7 +509,84 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
 
 // ---- k_hist_staged: class-count histograms -----------------------------------
 // Histogram layout in shared memory: [pl][B+1][C] int32, one spare bin per
-// projection, plus one trash histogram for padding positions.
+// projection, then a trash word.  Addresses are byte offsets clamped (as
+// unsigned) to the trash word, which absorbs padding positions (label offset
+// very negative), labels outside [0, C) and non-finite projected values.
+struct BinParams {
+  float mn, W, inv_w, c;
+  unsigned hb;  // byte base of the projection's histogram minus magic*C*4 (mod 2^32)
+  int fast;
+};
+
+template <int K>
+__device__ __forceinline__ void hist_tile(const float* __restrict__ s_tile, const int* __restrict__ s_y4,
+                                          const int16_t* drow, const float* dsg, int St, int lane, const BinParams& bp,
+                                          unsigned C4, unsigned limit, char* s_histb) {
+  int roff[K];
+  float2 sg[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    roff[j] = drow[j] * St + 2 * lane;
+    sg[j] = make_float2(dsg[j], dsg[j]);
+  }
+  const float2 inv2 = make_float2(bp.inv_w, bp.inv_w);
+  const float2 c2 = make_float2(bp.c, bp.c);
+  const float2 m2 = make_float2(kMagic, kMagic);
+  const float2 m1 = make_float2(1.0f - kMagic, 1.0f - kMagic);
+  for (int ps = 0; ps < St; ps += 64) {
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
+    const int2 y4 = *reinterpret_cast<const int2*>(s_y4 + ps + 2 * lane);
+    const float2 e = ffma2(acc, inv2, c2);
+    const float2 tq = fadd2(e, m2);
+    const float2 q1 = fadd2(tq, m1);
+    // t_{q+1} = min + (q+1)*W with two roundings (scalar: not fused)
+    const float tbx = __fadd_rn(bp.mn, __fmul_rn(q1.x, bp.W));
+    const float tby = __fadd_rn(bp.mn, __fmul_rn(q1.y, bp.W));
+    unsigned ax = __float_as_uint(tq.x) * C4 + (bp.hb + (unsigned)y4.x);
+    unsigned ay = __float_as_uint(tq.y) * C4 + (bp.hb + (unsigned)y4.y);
+    if (tbx <= acc.x) ax += C4;
+    if (tby <= acc.y) ay += C4;
+    ax = min(ax, limit);
+    ay = min(ay, limit);
+    atomicAdd(reinterpret_cast<int*>(s_histb + ax), 1);
+    atomicAdd(reinterpret_cast<int*>(s_histb + ay), 1);
+  }
+}
+
+template <int KMAX>
+__device__ __forceinline__ void hist_tile_k(int k, const float* s_tile, const int* s_y4, const int16_t* drow,
+                                            const float* dsg, int St, int lane, const BinParams& bp, unsigned C4,
+                                            unsigned limit, char* s_histb) {
+  switch (k) {
+#define SOF_H_CASE(N) \
+  case N:             \
+    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1)>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb); \
+    break;
+    SOF_H_CASE(1) SOF_H_CASE(2) SOF_H_CASE(3) SOF_H_CASE(4) SOF_H_CASE(5) SOF_H_CASE(6) SOF_H_CASE(7)
+    SOF_H_CASE(8) SOF_H_CASE(9) SOF_H_CASE(10) SOF_H_CASE(11) SOF_H_CASE(12) SOF_H_CASE(13) SOF_H_CASE(14)
+    SOF_H_CASE(15) SOF_H_CASE(16) SOF_H_CASE(17) SOF_H_CASE(18) SOF_H_CASE(19) SOF_H_CASE(20) SOF_H_CASE(21)
+    SOF_H_CASE(22) SOF_H_CASE(23) SOF_H_CASE(24) SOF_H_CASE(25) SOF_H_CASE(26) SOF_H_CASE(27) SOF_H_CASE(28)
+    SOF_H_CASE(29) SOF_H_CASE(30) SOF_H_CASE(31) SOF_H_CASE(32)
+#undef SOF_H_CASE
+    default:
+      break;
+  }
+}
+
+// exact estimate-and-correct rule for projections outside the fast condition
+__device__ __forceinline__ void hist_tile_slow(int k, const float* __restrict__ s_tile, const int* __restrict__ s_y4,
+                                               const int16_t* drow, const float* dsg, int St, int lane,
+                                               const BinParams& bp, int B, int C, int hbase, int32_t* s_hist) {
+  for (int i = lane; i < St; i += 32) {
+    float acc = 0.0f;
+    for (int j = 0; j < k; ++j) acc = __fmaf_rn(dsg[j], s_tile[drow[j] * St + i], acc);
+    const int y4 = s_y4[i];
+    if (y4 >= 0) atomicAdd(&s_hist[hbase + bin_of(acc, bp.mn, bp.W, bp.inv_w, B) * C + (y4 >> 2)], 1);
+  }
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, const int32_t* __restrict__ idx,
                                                               ProjView pv, StagedPlan sp, int B, int PG,
@@ -450,104 +595,80 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   const int nw = (ds.d + 31) >> 5;
   const int C = ds.C;
   const int HS = (B + 1) * C;  // words per projection histogram
+  const int hist_words = ((PG * HS + 1) + 3) & ~3;
   // every region starts on a 16-byte boundary (s_y4 is read as int2)
   float* s_tile = reinterpret_cast<float*>(s_raw);                        // [kStThreads*kStEpt]
-  int* s_y4 = reinterpret_cast<int*>(s_tile + kStThreads * kStEpt);       // [256] byte offset of the label
-  int32_t* s_hist = s_y4 + 256;                                           // [(PG+1)*HS]
-  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_hist + (((PG + 1) * HS + 3) & ~3));  // [nw]
+  int* s_y4 = reinterpret_cast<int*>(s_tile + kStThreads * kStEpt);       // [256] label byte offset
+  int32_t* s_hist = s_y4 + 256;                                           // [PG*HS + 1 (trash)]
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_hist + hist_words);    // [nw]
   int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                      // [nw]
   int* s_rowfeat = s_wpre + nw;                                           // [kStUMax]
-  int* s_dk = s_rowfeat + kStUMax;                                        // [PG]
-  float* s_dsg = reinterpret_cast<float*>(s_dk + 32);                     // [PG*KMAX]
-  int16_t* s_drow = reinterpret_cast<int16_t*>(s_dsg + 32 * KMAX);        // [PG*KMAX]
+  int* s_dk = s_rowfeat + kStUMax;                                        // [32]
+  float* s_dsg = reinterpret_cast<float*>(s_dk + 32);                     // [32*KMAX]
+  int16_t* s_drow = reinterpret_cast<int16_t*>(s_dsg + 32 * KMAX);        // [32*KMAX]
   __shared__ int s_misc[kStWarps + 1];
-  __shared__ float s_bp[32][5];  // per projection: mn, W, inv_w, c, fast flag
+  __shared__ BinParams s_bp[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = pv.P;
-  const int magic_bits = (int)__float_as_uint(kMagic);
+  const unsigned C4 = (unsigned)C * 4u;
+  const unsigned limit = (unsigned)(PG * HS) * 4u;  // byte offset of the trash word
+  const unsigned magic_bits = __float_as_uint(kMagic);
+  char* s_histb = reinterpret_cast<char*>(s_hist);
   const int64_t n_items = items_total(sp);
   for (int64_t t = blockIdx.x; t < n_items; t += gridDim.x) {
     const ItemPos it = decode_item(sp, t, P);
     const int64_t qbase = (int64_t)it.j * P + it.p0;
     __syncthreads();  // previous item's flush finished
-    for (int e = threadIdx.x; e < (PG + 1) * HS; e += kStThreads) s_hist[e] = 0;
+    {
+      int4* h4 = reinterpret_cast<int4*>(s_hist);
+      for (int e = threadIdx.x; e < hist_words / 4; e += kStThreads) h4[e] = make_int4(0, 0, 0, 0);
+    }
     const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
     build_desc<KMAX>(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_dk, s_drow, s_dsg);
     if (threadIdx.x < it.np) {
       const int pl = threadIdx.x;
       const float mn = key2f(mm[(it.h * P + it.p0 + pl) * 2]);
       const float mx = key2f(mm[(it.h * P + it.p0 + pl) * 2 + 1]);
-      const float W = bin_width(mn, mx, B);
-      const float inv_w = __frcp_rn(W);
-      const float c = __fsub_rn(__fmul_rn(-mn, inv_w), 0.75f);
+      BinParams bp;
+      bp.mn = mn;
+      bp.W = bin_width(mn, mx, B);
+      bp.inv_w = __frcp_rn(bp.W);
+      bp.c = __fsub_rn(__fmul_rn(-mn, bp.inv_w), 0.75f);
       const float M = fmaxf(fabsf(mn), fabsf(mx));
-      const bool fast = W > 0.0f && isfinite(inv_w) && isfinite(c) && M <= kCondLimit * W;
-      s_bp[pl][0] = mn;
-      s_bp[pl][1] = W;
-      s_bp[pl][2] = inv_w;
-      s_bp[pl][3] = c;
-      s_bp[pl][4] = fast ? 1.0f : 0.0f;
+      bp.fast = (bp.W > 0.0f && isfinite(bp.inv_w) && isfinite(bp.c) && M <= kCondLimit * bp.W) ? 1 : 0;
+      bp.hb = (unsigned)(pl * HS * 4) - magic_bits * C4;
+      s_bp[pl] = bp;
     }
-    __syncthreads();
+    const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
     const int64_t len = it.end - it.beg;
     if (U <= kStUMax) {
       const int St = choose_st(U);
       const int64_t ntile = (len + St - 1) / St;
       TileLoader ld;
-      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat);
-      int ylab = 0;
-      if (threadIdx.x < St) ylab = ld.valid ? (int)ds.y[ld.sid] : -1;
+      bool vec = contig && len >= St;
+      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat, vec);
       for (int64_t tt = 0; tt < ntile; ++tt) {
         __syncthreads();
-        ld.store(s_tile, St, U);
+        ld.store(s_tile, St, U, vec);
         if (threadIdx.x < St) {
-          // byte offset added to a projection's bin offset; padding and labels
-          // outside [0, C) go to the trash histogram
-          s_y4[threadIdx.x] = (ylab >= 0 && ylab < C) ? ylab * 4 : -1;
+          // labels outside [0, C) and padding: a very negative offset that the
+          // unsigned clamp sends to the trash word
+          s_y4[threadIdx.x] = (ld.ylab >= 0 && ld.ylab < C) ? ld.ylab * 4 : (INT_MIN / 2);
         }
         __syncthreads();
         if (tt + 1 < ntile) {
           const int64_t nb = it.beg + (tt + 1) * St;
-          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat);
-          if (threadIdx.x < St) ylab = ld.valid ? (int)ds.y[ld.sid] : -1;
+          vec = contig && (it.end - nb) >= St;
+          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat, vec);
         }
         for (int pl = warp; pl < it.np; pl += kStWarps) {
-          const int k = s_dk[pl];
-          const float mn = s_bp[pl][0], W = s_bp[pl][1], inv_w = s_bp[pl][2], c = s_bp[pl][3];
-          const bool fast = s_bp[pl][4] != 0.0f;
-          const int hbase4 = pl * HS * 4;                  // byte offset of the projection's histogram
-          const int trash4 = PG * HS * 4;
-          for (int ps = 0; ps < St; ps += 64) {
-            const int i0 = ps + 2 * lane;
-            float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int jj = 0; jj < KMAX; ++jj) {
-              if (jj < k) {
-                const float2 x = *reinterpret_cast<const float2*>(s_tile + s_drow[pl * KMAX + jj] * St + i0);
-                const float s = s_dsg[pl * KMAX + jj];
-                acc = ffma2(make_float2(s, s), x, acc);
-              }
-            }
-            const int2 y4 = *reinterpret_cast<const int2*>(s_y4 + i0);
-            int bx, by;
-            if (fast) {
-              const float2 e = ffma2(acc, make_float2(inv_w, inv_w), make_float2(c, c));
-              const float2 tq = fadd2(e, make_float2(kMagic, kMagic));
-              const float2 q1 = fadd2(tq, make_float2(1.0f - kMagic, 1.0f - kMagic));
-              const float2 tb = fadd2(make_float2(mn, mn), fmul2(q1, make_float2(W, W)));
-              bx = (int)__float_as_uint(tq.x) - magic_bits + (tb.x <= acc.x ? 1 : 0);
-              by = (int)__float_as_uint(tq.y) - magic_bits + (tb.y <= acc.y ? 1 : 0);
-            } else {
-              bx = bin_of(acc.x, mn, W, inv_w, B);
-              by = bin_of(acc.y, mn, W, inv_w, B);
-            }
-            // padding, labels outside [0, C) and (for non-finite input) bins
-            // outside [0, B] go to the trash histogram
-            const int ax = (y4.x >= 0 && (unsigned)bx <= (unsigned)B) ? hbase4 + bx * C * 4 + y4.x : trash4;
-            const int ay = (y4.y >= 0 && (unsigned)by <= (unsigned)B) ? hbase4 + by * C * 4 + y4.y : trash4;
-            atomicAdd(reinterpret_cast<int*>(reinterpret_cast<char*>(s_hist) + ax), 1);
-            atomicAdd(reinterpret_cast<int*>(reinterpret_cast<char*>(s_hist) + ay), 1);
-          }
+          const BinParams bp = s_bp[pl];
+          if (bp.fast)
+            hist_tile_k<KMAX>(s_dk[pl], s_tile, s_y4, s_drow + pl * KMAX, s_dsg + pl * KMAX, St, lane, bp, C4, limit,
+                              s_histb);
+          else
+            hist_tile_slow(s_dk[pl], s_tile, s_y4, s_drow + pl * KMAX, s_dsg + pl * KMAX, St, lane, bp, B, C, pl * HS,
+                           s_hist);
         }
       }
     } else {
@@ -557,7 +678,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         const int rb = pv.beg[q];
         int k = pv.end[q] - rb;
         k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
-        const float mn = s_bp[pl][0], W = s_bp[pl][1], inv_w = s_bp[pl][2];
+        const BinParams bp = s_bp[pl];
         for (int64_t e = it.beg + lane; e < it.end; e += 32) {
           const int64_t s = safe_sample(idx[e], ds.n);
           float acc = 0.0f;
@@ -568,39 +689,41 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
             acc = __fadd_rn(acc, pv.sign[rb + jj] == 1 ? x : -x);
           }
           const int yv = ds.y[s];
-          if (yv < C) atomicAdd(&s_hist[pl * HS + bin_of(acc, mn, W, inv_w, B) * C + yv], 1);
+          if (yv < C) atomicAdd(&s_hist[pl * HS + bin_of(acc, bp.mn, bp.W, bp.inv_w, B) * C + yv], 1);
         }
       }
     }
     __syncthreads();
     // flush: the spare bin B folds into bin B-1
     const int BC = B * C;
-    for (int e = threadIdx.x; e < it.np * BC; e += kStThreads) {
-      const int pl = e / BC;
-      const int r = e - pl * BC;
-      int v = s_hist[pl * HS + r];
-      if (r >= (B - 1) * C) v += s_hist[pl * HS + r + C];
-      if (v) atomicAdd(&hist[(it.h * P + it.p0 + pl) * (int64_t)BC + r], v);
+    for (int pl = warp; pl < it.np; pl += kStWarps) {
+      int32_t* g = hist + (it.h * P + it.p0 + pl) * (int64_t)BC;
+      const int32_t* h = s_hist + pl * HS;
+      for (int r = lane; r < BC; r += 32) {
+        int v = h[r];
+        if (r >= BC - C) v += h[r + C];
+        if (v) atomicAdd(&g[r], v);
+      }
     }
   }
 }
 
 // ---- host side ----------------------------------------------------------------
 int hist_group_size(int B, int C) {
-  // histogram shared memory <= 100 KB: (PG + 1) * (B + 1) * C * 4
+  // histogram shared memory <= 100 KB: PG * (B + 1) * C * 4
   int pg = 32;
-  while (pg > 1 && (size_t)(pg + 1) * (B + 1) * C * 4 > 100 * 1024) pg >>= 1;
+  while (pg > 1 && (size_t)pg * (B + 1) * C * 4 > 100 * 1024) pg >>= 1;
   return pg;
 }
 
 size_t mm_smem_bytes(int d, int kmax) {
   const int nw = (d + 31) >> 5;
-  return (size_t)kStThreads * kStEpt * 4 + (size_t)nw * 8 + kStUMax * 4 + kMmGroup * 4 +
-         (size_t)kMmGroup * kmax * 6 + 64;
+  return (size_t)kStThreads * kStEpt * 4 + (size_t)kMmGroup * 32 * 8 + (size_t)nw * 8 + kStUMax * 4 +
+         kMmGroup * 4 + (size_t)kMmGroup * kmax * 6 + 64;
 }
 size_t hist_smem_bytes(int d, int kmax, int B, int C, int PG) {
   const int nw = (d + 31) >> 5;
-  const size_t hist_words = ((size_t)(PG + 1) * (B + 1) * C + 3) & ~(size_t)3;
+  const size_t hist_words = ((size_t)PG * (B + 1) * C + 1 + 3) & ~(size_t)3;
   return (size_t)kStThreads * kStEpt * 4 + 256 * 4 + hist_words * 4 + (size_t)nw * 8 + kStUMax * 4 + 32 * 4 +
          (size_t)32 * kmax * 6 + 64;
 }
