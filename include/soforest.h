@@ -144,6 +144,29 @@ so_status so_split_search_batch(const so_dataset *ds, const int32_t *idx, int64_
                                 int64_t *left_counts_dev, void *workspace, size_t ws_bytes,
                                 void *stream);
 
+/* so_split_search without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running inside another framework's memory pool that owns
+ * the device memory, processes held to a fixed device-memory budget, and
+ * latency-critical loops where an allocation (and the device synchronisation
+ * cudaMalloc/cudaFree can imply) is not acceptable.  Same arguments and result
+ * as so_split_search, minus the workspace.
+ *
+ * Scratch: a statically allocated 8 MiB device array inside the library (every
+ * GPU that loads the library holds it until the process exits).  A node whose
+ * scratch (about n_proj * n_bins * n_classes * 4 bytes of histograms plus a
+ * few KiB) exceeds 8 MiB is rejected with SO_EINVAL before any launch.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the array and
+ * leaves its contents behind (the kernels initialise what they read); calls
+ * that overlap on the GPU, from any stream or thread, race on it.  Keep
+ * tracing (so_profile_enable) off: tracing creates CUDA events.  The call
+ * synchronises `stream`. */
+so_status so_split_search_noalloc(const so_dataset *ds, const int32_t *idx, int64_t n_node,
+                                  const so_projs *projs, const so_split_params *params,
+                                  so_split *out_host, int64_t *left_counts_host, void *stream);
+
 /* Device workspace bytes needed by the two calls above. */
 size_t so_split_search_ws_bytes(int32_t m, int64_t n_total, int32_t n_proj, int32_t n_classes,
                                 const so_split_params *params);

@@ -187,6 +187,12 @@ so_status guarded(F f) {
 
 }  // namespace
 
+namespace sof {
+// Sets the thread-local message returned by so_last_error() (for entry points
+// defined in other translation units).
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace sof
+
 extern "C" {
 
 const char* so_last_error(void) { return g_err.c_str(); }

@@ -83,6 +83,8 @@ _SIGS = {
                                C.POINTER(so_split_params), C.POINTER(so_split), _V, _V, _SZ, _V]),
     "so_split_search_batch": (_I32, [C.POINTER(so_dataset), _V, _I64, _V, _I32, C.POINTER(so_projs),
                                      C.POINTER(so_split_params), _V, _V, _V, _SZ, _V]),
+    "so_split_search_noalloc": (_I32, [C.POINTER(so_dataset), _V, _I64, C.POINTER(so_projs),
+                                       C.POINTER(so_split_params), C.POINTER(so_split), _V, _V]),
     "so_split_search_ws_bytes": (_SZ, [_I32, _I64, _I32, _I32, C.POINTER(so_split_params)]),
     "so_partition": (_I32, [C.POINTER(so_dataset), _V, _I64, _V, _V, _I32, _F, C.POINTER(C.c_int64), _V]),
     "so_partition_batch": (_I32, [C.POINTER(so_dataset), _V, _V, _I64, _V, _I32, C.POINTER(so_projs),
@@ -208,6 +210,19 @@ def so_split_search(ds: DeviceDataset, idx, projs: DeviceProjs, params: so_split
                                  lc.ctypes.data_as(C.c_void_p), _ptr(workspace),
                                  0 if workspace is None else workspace.numel() * workspace.element_size(),
                                  _stream(stream)))
+    return out, lc[:ds.n_classes].copy()
+
+
+def so_split_search_noalloc(ds: DeviceDataset, idx, projs: DeviceProjs, params: so_split_params, stream=None):
+    """One node with the library's static scratch (no device allocation).
+    Returns (so_split, left_counts numpy int64[C])."""
+    out = so_split()
+    lc = np.zeros(8, dtype=np.int64)
+    d = ds.c()
+    p = projs.c()
+    n = 0 if idx is None else int(idx.numel())
+    _check(lib().so_split_search_noalloc(C.byref(d), _ptr(idx), n, C.byref(p), C.byref(params), C.byref(out),
+                                         lc.ctypes.data_as(C.c_void_p), _stream(stream)))
     return out, lc[:ds.n_classes].copy()
 
 
