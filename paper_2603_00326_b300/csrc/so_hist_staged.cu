@@ -32,8 +32,10 @@ namespace sof {
 
 constexpr int kStThreads = 512;          // threads of the staged kernels (16 warps)
 constexpr int kStWarps = kStThreads / 32;
-constexpr int kStEpt = 32;               // staged elements per thread per tile (registers)
-constexpr int kStUMax = kStThreads * kStEpt / 64;  // rows of a tile at St = 64 -> 256
+constexpr int kStEpt = 32;               // staged elements per thread per tile (registers), histograms
+constexpr int kMmEpt = 16;               // the same for min / max (smaller tile: two CTAs per SM)
+constexpr int kStUMax = kStThreads * kStEpt / 64;  // rows of a histogram tile at St = 64 -> 256
+constexpr int kMmUMax = kStThreads * kMmEpt / 64;  // rows of a min / max tile at St = 64 -> 128
 constexpr int kStMaxWords = 2048;        // feature bitmap words (d <= 65536)
 constexpr int kMmPPW = 16;               // min/max: projections per warp
 constexpr int kMmGroup = kStWarps * kMmPPW;  // 256 projections per min/max group
@@ -196,8 +198,9 @@ __device__ __forceinline__ void build_desc(const ProjView& pv, int64_t qbase, in
 // one gather per element.  Vector form (a full tile of consecutive, 16-byte
 // aligned samples): thread owns float4 column tid % (St/4).  Threads tid < St
 // also fetch the label of tile position tid.
+template <int EPT>
 struct TileLoader {
-  float pre[kStEpt];
+  float pre[EPT];
   int ylab;  // label of position tid (tid < St), -1 for padding
   __device__ __forceinline__ void load(const DatasetView& ds, const int32_t* __restrict__ idx, int64_t tbeg,
                                        int64_t tend, int St, int U, const int* s_rowfeat, bool vec) {
@@ -208,7 +211,7 @@ struct TileLoader {
       const int rstep = kStThreads / nq;
       const int64_t sid0 = idx[tbeg];
 #pragma unroll
-      for (int k = 0; k < kStEpt / 4; ++k) {
+      for (int k = 0; k < EPT / 4; ++k) {
         const int r = r0 + k * rstep;
         if (r < U) {
           const float4 v = __ldg(reinterpret_cast<const float4*>(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid0) + q);
@@ -228,7 +231,7 @@ struct TileLoader {
       // padding positions repeat the tile's first sample (min / max unchanged)
       const int64_t sid = safe_sample(idx[valid ? pos : tbeg], ds.n);
 #pragma unroll
-      for (int k = 0; k < kStEpt; ++k) {
+      for (int k = 0; k < EPT; ++k) {
         const int r = r0 + k * rstep;
         if (r < U) pre[k] = __ldg(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid);
       }
@@ -242,7 +245,7 @@ struct TileLoader {
       const int r0 = threadIdx.x / nq;
       const int rstep = kStThreads / nq;
 #pragma unroll
-      for (int k = 0; k < kStEpt / 4; ++k) {
+      for (int k = 0; k < EPT / 4; ++k) {
         const int r = r0 + k * rstep;
         if (r < U)
           reinterpret_cast<float4*>(s_tile + r * St)[q] =
@@ -253,7 +256,7 @@ struct TileLoader {
       const int r0 = threadIdx.x / St;
       const int rstep = kStThreads / St;
 #pragma unroll
-      for (int k = 0; k < kStEpt; ++k) {
+      for (int k = 0; k < EPT; ++k) {
         const int r = r0 + k * rstep;
         if (r < U) s_tile[r * St + i] = pre[k];
       }
@@ -272,10 +275,11 @@ __device__ __forceinline__ bool item_contiguous(const DatasetView& ds, const int
   return __syncthreads_and(ok) != 0;
 }
 
+template <int EPT>
 __device__ __forceinline__ int choose_st(int U) {
-  // U * St <= kStThreads * kStEpt, St in {64, 128, 256}
-  if (U * 256 <= kStThreads * kStEpt) return 256;
-  if (U * 128 <= kStThreads * kStEpt) return 128;
+  // U * St <= kStThreads * EPT, St in {64, 128, 256}
+  if (U * 256 <= kStThreads * EPT) return 256;
+  if (U * 128 <= kStThreads * EPT) return 128;
   return 64;
 }
 
@@ -302,6 +306,13 @@ __global__ void __launch_bounds__(128) k_groups(const V4* plan_total, const int3
       const int umax = pass == 0 ? umax1 : umax2;
       const int pmax = pass == 0 ? pmax1 : pmax2;
       int32_t* gs = (pass == 0 ? gs1 : gs2) + h * (int64_t)(P + 1);
+      if (d <= umax) {
+        // every group fits the tile whatever its features: fixed chunks of pmax
+        const int ng = (P + pmax - 1) / pmax;
+        for (int g = lane; g <= ng; g += 32) gs[g] = min(g * pmax, P);
+        if (lane == 0) (pass == 0 ? ng1 : ng2)[h] = ng;
+        continue;
+      }
       int U = 0, cnt = 0, nset = 0, g = 0;
       if (lane == 0) gs[0] = 0;
       for (int p = 0; p < P; ++p) {
@@ -381,7 +392,7 @@ struct ItemScanF {
 // pair of the tile with the projection's rows and signs in registers (the
 // loop is specialised on the projection's non-zero count K); per-lane running
 // minima and maxima live in shared memory until the item ends.
-template <int K>
+template <int K, int NPS>
 __device__ __forceinline__ void mm_tile(const float* __restrict__ s_tile, const int16_t* drow, const float* dsg,
                                         int St, int lane, float& mn, float& mx) {
   int roff[K];
@@ -391,42 +402,67 @@ __device__ __forceinline__ void mm_tile(const float* __restrict__ s_tile, const 
     roff[j] = drow[j] * St + 2 * lane;
     sg[j] = make_float2(dsg[j], dsg[j]);
   }
-  for (int ps = 0; ps < St; ps += 64) {
-    float2 acc = make_float2(0.0f, 0.0f);
+  // NPS > 0: the St/64 pair-steps are unrolled (St = 64 * NPS); NPS = 0: rolled
+  const int nps = NPS > 0 ? NPS : (St >> 6);
 #pragma unroll
-    for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
-    mn = fminf(mn, fminf(acc.x, acc.y));
-    mx = fmaxf(mx, fmaxf(acc.x, acc.y));
+  for (int q = 0; q < (NPS > 0 ? NPS : 1); ++q) {
+    for (int r = 0; r < (NPS > 0 ? 1 : nps); ++r) {
+      const int ps = 64 * (NPS > 0 ? q : r);
+      float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
+      mn = fminf(mn, fminf(acc.x, acc.y));
+      mx = fmaxf(mx, fmaxf(acc.x, acc.y));
+    }
   }
 }
 
+// Dispatch on (non-zero count, pair-steps per tile); counts above 16 use the
+// rolled form.
 template <int KMAX>
 __device__ __forceinline__ void mm_tile_k(int k, const float* s_tile, const int16_t* drow, const float* dsg, int St,
                                           int lane, float& mn, float& mx) {
-  switch (k) {
-#define SOF_MM_CASE(N) \
-  case N:              \
-    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1)>(s_tile, drow, dsg, St, lane, mn, mx); \
-    break;
+  const int nps = St >> 6;
+  const int key = k * 8 + (nps == 4 ? 2 : nps == 2 ? 1 : 0);
+  switch (key) {
+#define SOF_MM_CASE(N)                                                                                        \
+  case N * 8 + 0:                                                                                             \
+    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 1>(s_tile, drow, dsg, St, lane, mn, mx);                      \
+    return;                                                                                                   \
+  case N * 8 + 1:                                                                                             \
+    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 2>(s_tile, drow, dsg, St, lane, mn, mx);                      \
+    return;                                                                                                   \
+  case N * 8 + 2:                                                                                             \
+    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 4>(s_tile, drow, dsg, St, lane, mn, mx);                      \
+    return;
     SOF_MM_CASE(1) SOF_MM_CASE(2) SOF_MM_CASE(3) SOF_MM_CASE(4) SOF_MM_CASE(5) SOF_MM_CASE(6) SOF_MM_CASE(7)
     SOF_MM_CASE(8) SOF_MM_CASE(9) SOF_MM_CASE(10) SOF_MM_CASE(11) SOF_MM_CASE(12) SOF_MM_CASE(13)
-    SOF_MM_CASE(14) SOF_MM_CASE(15) SOF_MM_CASE(16) SOF_MM_CASE(17) SOF_MM_CASE(18) SOF_MM_CASE(19)
-    SOF_MM_CASE(20) SOF_MM_CASE(21) SOF_MM_CASE(22) SOF_MM_CASE(23) SOF_MM_CASE(24) SOF_MM_CASE(25)
-    SOF_MM_CASE(26) SOF_MM_CASE(27) SOF_MM_CASE(28) SOF_MM_CASE(29) SOF_MM_CASE(30) SOF_MM_CASE(31)
-    SOF_MM_CASE(32)
+    SOF_MM_CASE(14) SOF_MM_CASE(15) SOF_MM_CASE(16)
 #undef SOF_MM_CASE
+    default:
+      break;
+  }
+  switch (k) {
+#define SOF_MM_ROLLED(N) \
+  case N:                \
+    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 0>(s_tile, drow, dsg, St, lane, mn, mx); \
+    break;
+    SOF_MM_ROLLED(17) SOF_MM_ROLLED(18) SOF_MM_ROLLED(19) SOF_MM_ROLLED(20) SOF_MM_ROLLED(21) SOF_MM_ROLLED(22)
+    SOF_MM_ROLLED(23) SOF_MM_ROLLED(24) SOF_MM_ROLLED(25) SOF_MM_ROLLED(26) SOF_MM_ROLLED(27) SOF_MM_ROLLED(28)
+    SOF_MM_ROLLED(29) SOF_MM_ROLLED(30) SOF_MM_ROLLED(31) SOF_MM_ROLLED(32)
+#undef SOF_MM_ROLLED
     default:
       break;
   }
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, const int32_t* __restrict__ idx,
+__global__ void __launch_bounds__(kStThreads, (KMAX <= 8 ? 2 : 1)) k_mm_staged(DatasetView ds, const int32_t* __restrict__ idx,
                                                             ProjView pv, StagedPlan sp, uint32_t* mm) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
-  float* s_tile = reinterpret_cast<float*>(s_raw);                       // [kStThreads*kStEpt]
-  float* s_pmin = s_tile + kStThreads * kStEpt;                          // [kMmGroup*32]
+  float* s_tile = reinterpret_cast<float*>(s_raw);                       // [kStThreads*kMmEpt]
+  float* s_pmin = s_tile + kStThreads * kMmEpt;                          // [kMmGroup*32]
   float* s_pmax = s_pmin + kMmGroup * 32;                                // [kMmGroup*32]
   uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_pmax + kMmGroup * 32);  // [nw]
   int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                     // [nw]
@@ -449,11 +485,11 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
       s_pmax[e] = -INFINITY;
     }
     const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
-    if (U <= kStUMax) {
-      const int St = choose_st(U);
+    if (U <= kMmUMax) {
+      const int St = choose_st<kMmEpt>(U);
       const int64_t len = it.end - it.beg;
       const int64_t ntile = (len + St - 1) / St;
-      TileLoader ld;
+      TileLoader<kMmEpt> ld;
       bool vec = contig && len >= St;
       ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat, vec);
       for (int64_t tt = 0; tt < ntile; ++tt) {
@@ -518,7 +554,7 @@ struct BinParams {
   int fast;
 };
 
-template <int K>
+template <int K, int NPS>
 __device__ __forceinline__ void hist_tile(const float* __restrict__ s_tile, const int* __restrict__ s_y4,
                                           const int16_t* drow, const float* dsg, int St, int lane, const BinParams& bp,
                                           unsigned C4, unsigned limit, char* s_histb) {
@@ -533,25 +569,30 @@ __device__ __forceinline__ void hist_tile(const float* __restrict__ s_tile, cons
   const float2 c2 = make_float2(bp.c, bp.c);
   const float2 m2 = make_float2(kMagic, kMagic);
   const float2 m1 = make_float2(1.0f - kMagic, 1.0f - kMagic);
-  for (int ps = 0; ps < St; ps += 64) {
-    float2 acc = make_float2(0.0f, 0.0f);
+  const int nps = NPS > 0 ? NPS : (St >> 6);
 #pragma unroll
-    for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
-    const int2 y4 = *reinterpret_cast<const int2*>(s_y4 + ps + 2 * lane);
-    const float2 e = ffma2(acc, inv2, c2);
-    const float2 tq = fadd2(e, m2);
-    const float2 q1 = fadd2(tq, m1);
-    // t_{q+1} = min + (q+1)*W with two roundings (scalar: not fused)
-    const float tbx = __fadd_rn(bp.mn, __fmul_rn(q1.x, bp.W));
-    const float tby = __fadd_rn(bp.mn, __fmul_rn(q1.y, bp.W));
-    unsigned ax = __float_as_uint(tq.x) * C4 + (bp.hb + (unsigned)y4.x);
-    unsigned ay = __float_as_uint(tq.y) * C4 + (bp.hb + (unsigned)y4.y);
-    if (tbx <= acc.x) ax += C4;
-    if (tby <= acc.y) ay += C4;
-    ax = min(ax, limit);
-    ay = min(ay, limit);
-    atomicAdd(reinterpret_cast<int*>(s_histb + ax), 1);
-    atomicAdd(reinterpret_cast<int*>(s_histb + ay), 1);
+  for (int q = 0; q < (NPS > 0 ? NPS : 1); ++q) {
+    for (int r = 0; r < (NPS > 0 ? 1 : nps); ++r) {
+      const int ps = 64 * (NPS > 0 ? q : r);
+      float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
+      const int2 y4 = *reinterpret_cast<const int2*>(s_y4 + ps + 2 * lane);
+      const float2 e = ffma2(acc, inv2, c2);
+      const float2 tq = fadd2(e, m2);
+      const float2 q1 = fadd2(tq, m1);
+      // t_{q+1} = min + (q+1)*W with two roundings (scalar: not fused)
+      const float tbx = __fadd_rn(bp.mn, __fmul_rn(q1.x, bp.W));
+      const float tby = __fadd_rn(bp.mn, __fmul_rn(q1.y, bp.W));
+      unsigned ax = __float_as_uint(tq.x) * C4 + (bp.hb + (unsigned)y4.x);
+      unsigned ay = __float_as_uint(tq.y) * C4 + (bp.hb + (unsigned)y4.y);
+      if (tbx <= acc.x) ax += C4;
+      if (tby <= acc.y) ay += C4;
+      ax = min(ax, limit);
+      ay = min(ay, limit);
+      atomicAdd(reinterpret_cast<int*>(s_histb + ax), 1);
+      atomicAdd(reinterpret_cast<int*>(s_histb + ay), 1);
+    }
   }
 }
 
@@ -559,17 +600,35 @@ template <int KMAX>
 __device__ __forceinline__ void hist_tile_k(int k, const float* s_tile, const int* s_y4, const int16_t* drow,
                                             const float* dsg, int St, int lane, const BinParams& bp, unsigned C4,
                                             unsigned limit, char* s_histb) {
-  switch (k) {
-#define SOF_H_CASE(N) \
-  case N:             \
-    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1)>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb); \
-    break;
+  const int nps = St >> 6;
+  const int key = k * 8 + (nps == 4 ? 2 : nps == 2 ? 1 : 0);
+  switch (key) {
+#define SOF_H_CASE(N)                                                                                               \
+  case N * 8 + 0:                                                                                                   \
+    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 1>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb);    \
+    return;                                                                                                         \
+  case N * 8 + 1:                                                                                                   \
+    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 2>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb);    \
+    return;                                                                                                         \
+  case N * 8 + 2:                                                                                                   \
+    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 4>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb);    \
+    return;
     SOF_H_CASE(1) SOF_H_CASE(2) SOF_H_CASE(3) SOF_H_CASE(4) SOF_H_CASE(5) SOF_H_CASE(6) SOF_H_CASE(7)
     SOF_H_CASE(8) SOF_H_CASE(9) SOF_H_CASE(10) SOF_H_CASE(11) SOF_H_CASE(12) SOF_H_CASE(13) SOF_H_CASE(14)
-    SOF_H_CASE(15) SOF_H_CASE(16) SOF_H_CASE(17) SOF_H_CASE(18) SOF_H_CASE(19) SOF_H_CASE(20) SOF_H_CASE(21)
-    SOF_H_CASE(22) SOF_H_CASE(23) SOF_H_CASE(24) SOF_H_CASE(25) SOF_H_CASE(26) SOF_H_CASE(27) SOF_H_CASE(28)
-    SOF_H_CASE(29) SOF_H_CASE(30) SOF_H_CASE(31) SOF_H_CASE(32)
+    SOF_H_CASE(15) SOF_H_CASE(16)
 #undef SOF_H_CASE
+    default:
+      break;
+  }
+  switch (k) {
+#define SOF_H_ROLLED(N) \
+  case N:               \
+    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 0>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb); \
+    break;
+    SOF_H_ROLLED(17) SOF_H_ROLLED(18) SOF_H_ROLLED(19) SOF_H_ROLLED(20) SOF_H_ROLLED(21) SOF_H_ROLLED(22)
+    SOF_H_ROLLED(23) SOF_H_ROLLED(24) SOF_H_ROLLED(25) SOF_H_ROLLED(26) SOF_H_ROLLED(27) SOF_H_ROLLED(28)
+    SOF_H_ROLLED(29) SOF_H_ROLLED(30) SOF_H_ROLLED(31) SOF_H_ROLLED(32)
+#undef SOF_H_ROLLED
     default:
       break;
   }
@@ -642,9 +701,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
     const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
     const int64_t len = it.end - it.beg;
     if (U <= kStUMax) {
-      const int St = choose_st(U);
+      const int St = choose_st<kStEpt>(U);
       const int64_t ntile = (len + St - 1) / St;
-      TileLoader ld;
+      TileLoader<kStEpt> ld;
       bool vec = contig && len >= St;
       ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat, vec);
       for (int64_t tt = 0; tt < ntile; ++tt) {
@@ -718,7 +777,7 @@ int hist_group_size(int B, int C) {
 
 size_t mm_smem_bytes(int d, int kmax) {
   const int nw = (d + 31) >> 5;
-  return (size_t)kStThreads * kStEpt * 4 + (size_t)kMmGroup * 32 * 8 + (size_t)nw * 8 + kStUMax * 4 +
+  return (size_t)kStThreads * kMmEpt * 4 + (size_t)kMmGroup * 32 * 8 + (size_t)nw * 8 + kStUMax * 4 +
          kMmGroup * 4 + (size_t)kMmGroup * kmax * 6 + 64;
 }
 size_t hist_smem_bytes(int d, int kmax, int B, int C, int PG) {
@@ -755,7 +814,7 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
       if (e != cudaSuccess) return e;
     }
     ProfScope ps_("k_groups", st);
-    k_groups<<<di.num_sms * 2, 128, smem, st>>>(plan_total, hist_nodes, a.pv, d, kStUMax, kMmGroup, kStUMax, PG,
+    k_groups<<<di.num_sms * 2, 128, smem, st>>>(plan_total, hist_nodes, a.pv, d, kMmUMax, kMmGroup, kStUMax, PG,
                                                 ss.ng1, ss.gs1, ss.ng2, ss.gs2);
   }
   ItemScanF isf{plan_total, hist_nodes, a.node_off, ss.ng1, ss.ng2, S, ss.item_off1, ss.item_off2};
