@@ -126,7 +126,7 @@ def cpu_baseline(ds, pr, n_sample_proj: int):
     return ds.n * n_sample_proj / dt, dt
 
 
-def extra_legs(S, torch, dev):
+def extra_legs(S, torch, dev, forest_trees=2):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
     64 projections/node, T=1024), and one tree grown to purity (tree_small)."""
@@ -204,6 +204,23 @@ def extra_legs(S, torch, dev):
         times.append(time.perf_counter() - t0)
     out["tree_small"] = {"train_s": min(times), "median_s": statistics.median(times), "nodes": tr.n_nodes,
                          "depth": int(tr.depth.max())}
+    del dd, root
+    if forest_trees > 0:
+        from paper_2603_00326_b300 import forest as F
+        fs = G.forest_2m()
+        fp = G.WORKLOAD_PARAMS["forest_2m"]
+        dd = S.DeviceDataset(torch.from_numpy(fs.X).to(dev), torch.from_numpy(fs.y).to(dev), 2)
+        cfg = F.ForestConfig(n_trees=forest_trees, n_proj=fp["n_proj"], lam=fp["lam"], cap=fp["cap"],
+                             sort_below=fp["sort_below"])
+        F.train_forest(F.ForestConfig(n_trees=1, n_proj=8, lam=1.5, cap=8), dd)  # warm-up
+        torch.cuda.synchronize()
+        trees, secs = F.train_forest(cfg, dd)
+        out["forest_2m"] = {"trees": forest_trees, "of": fp["n_trees"], "train_s": secs,
+                            "s_per_tree": secs / forest_trees,
+                            "projected_forest_s": secs / forest_trees * fp["n_trees"],
+                            "mean_nodes": float(np.mean([t.n_nodes for t in trees])),
+                            "max_depth": int(max(int(t.depth.max()) for t in trees))}
+        del dd
     return out
 
 
@@ -365,7 +382,7 @@ def run_ours(args):
                   "n_left": int(rec["n_left"])},
     }
     if rank == 0 and world == 1 and not args.no_extras:
-        line["extras"] = extra_legs(S, torch, dev)
+        line["extras"] = extra_legs(S, torch, dev, args.forest_trees)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt = cpu_baseline(ds_np, pr, 32)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -387,7 +404,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
-    ap.add_argument("--no-extras", action="store_true", help="skip the frontier and tree legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the frontier, tree and forest legs")
+    ap.add_argument("--forest-trees", type=int, default=2,
+                    help="trees of the n=2M, d=256 forest timed in the extras (0 skips)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -266,12 +266,19 @@ so_status so_train_tree(const so_dataset *ds, const int32_t *root_idx, int64_t n
 
 void so_tree_free(so_tree *tree);
 
-/* Measures the exact-sort and histogram paths on synthetic nodes drawn from
- * ds on this GPU and writes into params->sort_below the node size above
- * which the histogram path is faster (the paper's start-up microbenchmark,
- * Section 3.1).  Other fields of params are kept.  Synchronises `stream`. */
-so_status so_autotune(const so_dataset *ds, int32_t n_proj, so_split_params *params,
-                      void *stream);
+/* The start-up crossover microbenchmark of Section 3.1: on this GPU, for node
+ * sizes s = 32 .. 2047, times one batched split search of many s-sample nodes
+ * drawn from ds on the exact path and on the histogram path (n_proj sampled
+ * projections per node with nnz = min(nnz_cap, d, 1+Poisson(lambda))), and
+ * writes into params->sort_below the smallest measured size at which the
+ * histogram path is no slower per node (2048 if it never is).  Other fields
+ * of params are kept.  Times per size go to times_ms_host [2*n_sizes] when
+ * not NULL (exact, histogram), with the sizes in sizes_host [n_sizes];
+ * n_sizes_out receives the count (at most 16).  Takes well under a second;
+ * synchronises `stream`; uses the internal arena. */
+so_status so_autotune(const so_dataset *ds, int32_t n_proj, double lambda, int32_t nnz_cap,
+                      so_split_params *params, int32_t *sizes_host, float *times_ms_host,
+                      int32_t *n_sizes_out, void *stream);
 
 /* ---- tracing ------------------------------------------------------------
  * Per-stage timing (the paper instruments every node, Section 3).  When

@@ -745,12 +745,110 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
   });
 }
 
-so_status so_autotune(const so_dataset* ds, int32_t n_proj, so_split_params* params, void* stream) {
+so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32_t nnz_cap,
+                      so_split_params* params, int32_t* sizes_host, float* times_ms_host, int32_t* n_sizes_out,
+                      void* stream) {
   return guarded([&]() -> so_status {
     so_status st;
     if ((st = check_dataset(ds)) || (st = check_params(params))) return st;
     if (n_proj < 1 || n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj outside 1..1024");
-    return fail(SO_EINTERNAL, "autotuner not available in this build");
+    if (nnz_cap < 1 || nnz_cap > kMaxCap) return fail(SO_EINVAL, "nnz_cap outside 1..32");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SO_EINVAL, "lambda must be finite and >= 0");
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int C = ds->n_classes, P = n_proj, cap = nnz_cap, B = params->n_bins;
+    static const int kSizes[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2047};
+    const int n_sizes = (int)(sizeof(kSizes) / sizeof(kSizes[0]));
+    // nodes per size: enough work to time, bounded by the data
+    const int64_t budget = std::min<int64_t>(ds->n, (int64_t)1 << 18);
+    // histograms of every node must fit 256 MB in the histogram-only pass
+    const int64_t hist_nodes_max =
+        std::max<int64_t>(1, ((int64_t)256 << 20) / ((int64_t)P * B * C * 4 + 64));
+    auto nodes_for = [&](int s) {
+      return (int32_t)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(4096, hist_nodes_max), budget / s));
+    };
+    int32_t mcap = 1;
+    for (int si = 0; si < n_sizes; ++si) mcap = std::max<int32_t>(mcap, nodes_for(kSizes[si]));
+    const int64_t ncap = (int64_t)mcap * kSizes[n_sizes - 1] + budget;
+    auto layout = [&](Carver& cv, int32_t** idx, int64_t** off, uint64_t** keys, int32_t** snnz, int32_t** sbeg,
+                      int32_t** send, int32_t** sfeat, int8_t** ssign, so_split** out, SearchScratch* ss) {
+      *idx = cv.take<int32_t>(ncap);
+      *off = cv.take<int64_t>(mcap + 1);
+      *keys = cv.take<uint64_t>(mcap);
+      *snnz = cv.take<int32_t>((size_t)mcap * P);
+      *sbeg = cv.take<int32_t>((size_t)mcap * P);
+      *send = cv.take<int32_t>((size_t)mcap * P);
+      *sfeat = cv.take<int32_t>((size_t)mcap * P * cap);
+      *ssign = cv.take<int8_t>((size_t)mcap * P * cap);
+      *out = cv.take<so_split>(mcap);
+      carve_search(cv, *ss, mcap, ncap, P, C, B, kMaxSortBelow, 1);  // histogram scratch for every node
+    };
+    int32_t *idx, *snnz, *sbeg, *send, *sfeat;
+    int64_t* off;
+    uint64_t* keys;
+    int8_t* ssign;
+    so_split* out;
+    SearchScratch ss;
+    Carver dry;
+    dry.dry = true;
+    layout(dry, &idx, &off, &keys, &snnz, &sbeg, &send, &sfeat, &ssign, &out, &ss);
+    ArenaLease lease;
+    if ((st = lease.acquire(dry.used + 4096, cs))) return st;
+    Carver cv;
+    cv.base = (char*)lease.ptr();
+    cv.cap = lease.cap();
+    layout(cv, &idx, &off, &keys, &snnz, &sbeg, &send, &sfeat, &ssign, &out, &ss);
+    if (!cv.ok()) return fail(SO_ENOMEM, "arena too small");
+    cudaEvent_t e0, e1;
+    SO_CK(cudaEventCreate(&e0));
+    SO_CK(cudaEventCreate(&e1));
+    int best = kMaxSortBelow;
+    int found = 0;
+    for (int si = 0; si < n_sizes; ++si) {
+      const int s = kSizes[si];
+      const int32_t m = nodes_for(s);
+      SO_CK(launch_bench_nodes(m, s, ds->n, 0x5EEDull + (uint64_t)si, idx, off, keys, cs));
+      SO_CK(launch_sample(m, keys, P, ds->d, lambda, cap, snnz, sfeat, ssign, sbeg, send, cs));
+      float tms[2] = {0.0f, 0.0f};
+      for (int path = 0; path < 2; ++path) {
+        SearchArgs a;
+        a.ds = view_of(ds);
+        a.idx = idx;
+        a.n_total = (int64_t)m * s;
+        a.node_off = off;
+        a.m = m;
+        a.pv = ProjView{sbeg, send, sfeat, ssign, P};
+        a.B = B;
+        a.T = path == 0 ? kMaxSortBelow : 0;
+        a.hist_only = path == 1 ? 1 : 0;
+        a.eps = effective_eps(params->rescore_rel_eps, C);
+        a.max_nnz = cap;
+        a.out = out;
+        a.left_counts = nullptr;
+        SO_CK(launch_search(a, ss, cs));  // warm-up
+        SO_CK(cudaEventRecord(e0, cs));
+        const int reps = 3;
+        for (int r = 0; r < reps; ++r) SO_CK(launch_search(a, ss, cs));
+        SO_CK(cudaEventRecord(e1, cs));
+        SO_CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        SO_CK(cudaEventElapsedTime(&ms, e0, e1));
+        tms[path] = ms / reps / (float)m;  // per node
+      }
+      if (sizes_host) sizes_host[si] = s;
+      if (times_ms_host) {
+        times_ms_host[2 * si] = tms[0];
+        times_ms_host[2 * si + 1] = tms[1];
+      }
+      if (!found && tms[1] <= tms[0]) {
+        best = s;
+        found = 1;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_sizes_out) *n_sizes_out = n_sizes;
+    params->sort_below = best;
+    return SO_OK;
   });
 }
 

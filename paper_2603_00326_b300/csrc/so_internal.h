@@ -194,6 +194,8 @@ cudaError_t launch_part_nodes_from_splits(const int64_t* node_off, int32_t m, co
 cudaError_t launch_part_single(int64_t n, int32_t nnz, float thr, PartNode* node,
                                int64_t* node_off, cudaStream_t st);
 cudaError_t launch_fill_off(int64_t* off, int64_t n, cudaStream_t st);
+cudaError_t launch_bench_nodes(int32_t m, int32_t s, int64_t n, uint64_t seed, int32_t* idx, int64_t* off,
+                               uint64_t* keys, cudaStream_t st);
 cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, float* gain_tmp,
                                 cudaStream_t st);
 // scan tile sums needed for n elements (tile = 2048 elements)

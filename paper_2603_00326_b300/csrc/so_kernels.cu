@@ -1366,6 +1366,24 @@ __global__ void k_fill_off(int64_t* off, int64_t n) {
   off[0] = 0;
   off[1] = n;
 }
+// Synthetic nodes for the crossover benchmark: m nodes of s samples each,
+// indices drawn by splitmix64 from [0, n) and sorted within each node by a
+// per-node odd-even pass (order only affects memory locality), offsets j*s.
+__global__ void k_bench_nodes(int32_t m, int32_t s, int64_t n, uint64_t seed, int32_t* idx, int64_t* off,
+                              uint64_t* keys) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)m * s) idx[t] = (int32_t)(sm64(seed + (uint64_t)t) % (uint64_t)n);
+  if (t <= m) off[t] = (int64_t)t * s;
+  if (t < m) keys[t] = sm64(seed ^ (0xA5A5A5A5ull + (uint64_t)t));
+}
+cudaError_t launch_bench_nodes(int32_t m, int32_t s, int64_t n, uint64_t seed, int32_t* idx, int64_t* off,
+                               uint64_t* keys, cudaStream_t st) {
+  const int64_t tot = std::max<int64_t>((int64_t)m * s, m + 1);
+  ProfScope ps_("k_bench_nodes", st);
+  k_bench_nodes<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m, s, n, seed, idx, off, keys);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill_off(int64_t* off, int64_t n, cudaStream_t st) {
   {
     ProfScope ps_("k_fill_off", st);

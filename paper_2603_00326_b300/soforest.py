@@ -95,7 +95,7 @@ _SIGS = {
     "so_train_tree": (_I32, [C.POINTER(so_dataset), _V, _I64, C.POINTER(so_tree_params),
                              C.POINTER(so_tree), _V]),
     "so_tree_free": (None, [C.POINTER(so_tree)]),
-    "so_autotune": (_I32, [C.POINTER(so_dataset), _I32, C.POINTER(so_split_params), _V]),
+    "so_autotune": (_I32, [C.POINTER(so_dataset), _I32, _D, _I32, C.POINTER(so_split_params), _V, _V, _V, _V]),
     "so_last_error": (C.c_char_p, []),
     "so_shutdown": (None, []),
     "so_version": (C.c_char_p, []),
@@ -351,7 +351,13 @@ def so_train_tree(ds: DeviceDataset, root_idx, params: so_tree_params, stream=No
         lib().so_tree_free(C.byref(t))
 
 
-def so_autotune(ds: DeviceDataset, n_proj: int, params: so_split_params, stream=None) -> so_split_params:
+def so_autotune(ds: DeviceDataset, n_proj: int, lam: float, cap: int, params: so_split_params, stream=None):
+    """Crossover microbenchmark; sets params.sort_below.  Returns (params, sizes, times_ms[n,2])."""
     d = ds.c()
-    _check(lib().so_autotune(C.byref(d), n_proj, C.byref(params), _stream(stream)))
-    return params
+    sizes = np.zeros(16, dtype=np.int32)
+    times = np.zeros(32, dtype=np.float32)
+    k = C.c_int32(0)
+    _check(lib().so_autotune(C.byref(d), n_proj, lam, cap, C.byref(params), sizes.ctypes.data_as(C.c_void_p),
+                             times.ctypes.data_as(C.c_void_p), C.byref(k), _stream(stream)))
+    n = int(k.value)
+    return params, sizes[:n].copy(), times[:2 * n].reshape(n, 2).copy()

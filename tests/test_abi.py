@@ -108,3 +108,13 @@ def test_workspace_size_query_is_host_only(L):
     big = S.so_split_search_ws_bytes(1, 4 << 20, 256, 3, p)
     assert 0 < small < big
     assert big >= 256 * 256 * 3 * 4  # one node's histograms at least
+
+
+def test_autotune_argument_checks(L):
+    from paper_2603_00326_b300 import soforest as S
+    ds = _fake_dataset()
+    p = S.split_params()
+    k = C.c_int32(0)
+    for args in ((0, 1.5, 8), (8, -1.0, 8), (8, 1.5, 0), (8, 1.5, 33)):
+        assert L.so_autotune(C.byref(ds), args[0], args[1], args[2], C.byref(p), None, None, C.byref(k),
+                             None) == S.SO_EINVAL

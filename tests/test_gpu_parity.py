@@ -385,3 +385,38 @@ def test_frontier_1m_full_size(S):
         r = O.split_search(ds_np.X, ds_np.y, 2, idx[off[j]:off[j + 1]], q.ptr, q.feat, q.sign,
                            sort_below=p["sort_below"])
         U.assert_split_equal(rec[j], r, f"node {j}")
+
+
+# ---------------------------------------------------------------- crossover autotune
+
+def test_autotune_crossover_and_tree_with_tuned_T(S):
+    """The start-up microbenchmark returns a crossover within the supported
+    range; a tree grown with that T is still identical to the oracle's tree
+    grown with the same T."""
+    ds_np = G.tree_small(n=20000, d=16, seed=55)
+    ds = U.upload_dataset(ds_np.X, ds_np.y, 2)
+    prm, sizes, times = S.so_autotune(ds, 16, 1.5, 8, S.split_params(256, 1024, False))
+    T = prm.sort_below
+    assert 32 <= T <= 2048
+    assert len(sizes) >= 8 and np.all(times > 0)
+    root = G.all_indices(ds_np.n)
+    gt, ot = _train_both(S, ds_np.X, ds_np.y, 2, root, n_proj=16, lam=1.5, cap=8, sort_below=T, seed=3)
+    U.assert_tree_equal(gt, ot)
+
+
+# ---------------------------------------------------------------- forest
+
+def test_forest_bootstrap_trees_match_oracle(S):
+    """A small forest (lognormal heavy-tailed features, 8-sparse median-centred
+    labels, 10% flips): every bootstrapped tree identical to the oracle's."""
+    from paper_2603_00326_b300 import forest as F
+    ds_np = G.forest_2m(n=6000, d=32, seed=91)
+    ds = U.upload_dataset(ds_np.X, ds_np.y, 2)
+    cfg = F.ForestConfig(n_trees=4, n_proj=16, lam=1.5, cap=8, sort_below=512)
+    trees, _ = F.train_forest(cfg, ds)
+    assert len(trees) == 4
+    for t, gt in enumerate(trees):
+        root = F.root_indices(ds_np.n, t, cfg)
+        ot = O.train_tree(ds_np.X, ds_np.y, 2, root, n_proj=16, lam=1.5, cap=8, sort_below=512, seed=cfg.seed,
+                          tree_id=t)
+        U.assert_tree_equal(gt, ot)
