@@ -126,12 +126,14 @@ def cpu_baseline(ds, pr, n_sample_proj: int):
     return ds.n * n_sample_proj / dt, dt
 
 
-def extra_legs(S, torch, dev, forest_trees=2):
+def extra_legs(S, torch, dev, forest_trees=2, only=None):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
     64 projections/node, T=1024), and one tree grown to purity (tree_small)."""
     from paper_2603_00326_b300 import datagen as G
     out = {}
+    if only not in (None, "frontier"):
+        return _later_legs(S, torch, dev, forest_trees, only, out)
     ds_np = G.frontier_1m()
     p = G.WORKLOAD_PARAMS["frontier_1m"]
     idx_np, off_np = G.frontier_nodes(ds_np.n, p["n_nodes"])
@@ -189,6 +191,13 @@ def extra_legs(S, torch, dev, forest_trees=2):
                           "speedup": plain_ms / batched_ms, "identical": bool(same),
                           "batched_sample_projections_per_s": sp / (batched_ms / 1000.0)}
     del dd, idx, off, ws, outb, views
+    if only == "frontier":
+        return out
+    return _later_legs(S, torch, dev, forest_trees, only, out)
+
+
+def _later_legs(S, torch, dev, forest_trees, only, out):
+    from paper_2603_00326_b300 import datagen as G
     # one tree to purity
     ts = G.tree_small()
     tp = G.WORKLOAD_PARAMS["tree_small"]
@@ -205,7 +214,7 @@ def extra_legs(S, torch, dev, forest_trees=2):
     out["tree_small"] = {"train_s": min(times), "median_s": statistics.median(times), "nodes": tr.n_nodes,
                          "depth": int(tr.depth.max())}
     del dd, root
-    if forest_trees > 0:
+    if forest_trees > 0 and only in (None, "forest"):
         from paper_2603_00326_b300 import forest as F
         fs = G.forest_2m()
         fp = G.WORKLOAD_PARAMS["forest_2m"]
@@ -222,6 +231,18 @@ def extra_legs(S, torch, dev, forest_trees=2):
                             "max_depth": int(max(int(t.depth.max()) for t in trees))}
         del dd
     return out
+
+
+def run_leg(args):
+    """One secondary leg alone (for profiling): frontier | tree | forest."""
+    import torch
+    from paper_2603_00326_b300 import soforest as S
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    S.lib()
+    out = extra_legs(S, torch, dev, args.forest_trees if args.leg == "forest" else 0, only=args.leg)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -405,11 +426,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the frontier, tree and forest legs")
+    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest"],
+                    help="run one secondary leg alone and print its JSON")
     ap.add_argument("--forest-trees", type=int, default=2,
                     help="trees of the n=2M, d=256 forest timed in the extras (0 skips)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        return run_leg(args)
     return run_ours(args)
 
 
