@@ -134,9 +134,11 @@ so_status check_projs(const so_projs* pr) {
 }
 
 // The float gain's relative error is below (C+6) 2^-24; the re-score window
-// must exceed twice that so the double winner always enters the re-score.
+// must exceed three times that: the double winner then always enters the
+// re-score, and every projection holding a double tie of it keeps its float
+// maximum within the window.
 float effective_eps(float eps, int C) {
-  const float floor_eps = 2.5f * (float)(C + 6) * 5.9604645e-8f;
+  const float floor_eps = 3.5f * (float)(C + 6) * 5.9604645e-8f;
   if (!(eps > 0.0f)) eps = 4e-6f;
   return eps < floor_eps ? floor_eps : eps;
 }
@@ -541,7 +543,8 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
     const int64_t Mcap = n_root / 2 + 2;
     const int64_t Ncap = 2 * n_root + 1;
     // batch of nodes searched at once: bounded projection slots and histograms
-    const size_t per_node_proj = (size_t)P * ((size_t)cap * 5 + 12);
+    // sampled slots and the exact path's per-(node, projection) results
+    const size_t per_node_proj = (size_t)P * ((size_t)cap * 5 + 12 + sort_res_bytes());
     int64_t Mb = (int64_t)((size_t)512 << 20) / (int64_t)per_node_proj;
     if (HO) {
       const size_t per_hist = (size_t)P * B * C * 4 + (size_t)P * 16;

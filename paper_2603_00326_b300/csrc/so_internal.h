@@ -111,6 +111,8 @@ struct SearchScratch {
   int32_t* node_counts = nullptr;  // [m_hist_cap*C]
   int32_t* hist = nullptr;      // [m_hist_cap*P*B*C]
   int32_t* err = nullptr;       // [m+1] per-node bad-input flags
+  void* sort_res = nullptr;     // [m*P] per-(exact-path node, projection) results
+  int32_t* node_cls = nullptr;  // [m*8] class counts of exact-path nodes
   int64_t m_hist_cap = 0;
   StagedScratch staged;
 };
@@ -141,6 +143,12 @@ struct DeviceInfo {
 const DeviceInfo& device_info();
 
 cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStream_t st);
+
+// exact path: one warp per (node, projection); res holds m*P per-projection
+// results (sort_res_bytes() each), indexed by node
+cudaError_t launch_sort_warp(const SearchArgs& a, const V4* plan_total, const int32_t* tiny, const int32_t* med,
+                             void* res, int32_t* node_cls, cudaStream_t st);
+size_t sort_res_bytes();
 
 // staged-tile histogram path (features up to 65536)
 bool staged_supported(int d);
@@ -198,8 +206,8 @@ cudaError_t launch_bench_nodes(int32_t m, int32_t s, int64_t n, uint64_t seed, i
                                uint64_t* keys, cudaStream_t st);
 cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, float* gain_tmp,
                                 cudaStream_t st);
-// scan tile sums needed for n elements (tile = 2048 elements)
-inline int64_t scan_tiles_for_host(int64_t n) { return (n + 2047) / 2048 + 1; }
+// scan tile sums needed for n elements (tile = 512 elements)
+inline int64_t scan_tiles_for_host(int64_t n) { return (n + 511) / 512 + 1; }
 
 // ---- sampler ----------------------------------------------------------------
 cudaError_t launch_sample(int32_t m, const uint64_t* keys, int32_t P, int32_t d, double lambda,

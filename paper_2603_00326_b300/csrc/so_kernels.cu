@@ -13,9 +13,7 @@
 //               gain of every boundary, the projection's best (Section 3 step 3)
 //   k_hist_select per node: double re-score of the float near-ties, the
 //               lexicographic best (the paper's second GPU kernel)
-//   k_sort_tiny / k_sort_medium  exact path for small nodes: projected values
-//               sorted per projection, class prefix counts, Gini at every
-//               boundary between distinct values, float scan + double re-score
+//   (exact path for small nodes: so_sort_warp.cu)
 // plus the device sampler (Appendix A), the stable partition, and the
 // breadth-first frontier bookkeeping of tree growth.
 #include <algorithm>
@@ -103,7 +101,8 @@ struct PlanF {
   so_split* out;
   int64_t* left_counts;
 
-  // kind: 0 histogram, 1 tiny sort, 2 medium sort, 3 skip
+  // kind: 0 histogram, 1 exact path in registers (<= 512 samples),
+  // 2 exact path in shared memory (513 .. T-1 samples), 3 skip
   // a node whose rows are malformed or whose segment leaves [0, n_total) is skipped
   __device__ bool is_bad(int64_t j) const {
     const int64_t b = off[j], e = off[j + 1];
@@ -113,7 +112,7 @@ struct PlanF {
     if (is_bad(j)) return 3;
     if (force_hist) return nv >= 1 ? 0 : 3;
     if (nv < 2) return 3;
-    if (!hist_only && nv < T) return nv <= 32 ? 1 : 2;
+    if (!hist_only && nv < T) return nv <= 512 ? 1 : 2;
     return 0;
   }
   __device__ V4 value(int64_t j) const {
@@ -488,362 +487,6 @@ __global__ void k_hist_export(const V4* plan_total, const int32_t* hist_nodes, i
 }
 
 // ============================================================================
-// K3: exact path (sort) for small nodes
-// ============================================================================
-// Packed class counters: 16-bit fields, classes 0-3 in lo, 4-7 in hi.
-struct Packed {
-  unsigned long long lo, hi;
-};
-__device__ __forceinline__ void packed_add(Packed& a, int y) {
-  if (y < 4) a.lo += 1ull << (16 * y);
-  else a.hi += 1ull << (16 * (y - 4));
-}
-__device__ __forceinline__ int packed_get(const Packed& a, int c) {
-  return (int)(((c < 4 ? a.lo >> (16 * c) : a.hi >> (16 * (c - 4)))) & 0xFFFFull);
-}
-
-__device__ __forceinline__ unsigned long long sort_key(float v, int y) {
-  return ((unsigned long long)f2key(v) << 32) | (unsigned long long)(unsigned)y;
-}
-
-// Tiny nodes (2..32 samples): one warp per node, one sample per lane.
-__device__ __forceinline__ unsigned long long warp_bitonic32(unsigned long long val, int lane) {
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const unsigned long long o = __shfl_xor_sync(0xffffffffu, val, j);
-      const bool up = (lane & k) == 0;
-      const bool lower = (lane & j) == 0;
-      const unsigned long long mnv = val < o ? val : o;
-      const unsigned long long mxv = val < o ? o : val;
-      val = (lower == up) ? mnv : mxv;
-    }
-  }
-  return val;
-}
-
-struct TinyEval {
-  // after sort: lane i holds sorted element i
-  unsigned long long val;
-  int L[kMaxClasses];
-  bool cand;
-  float g32;
-};
-
-__device__ __forceinline__ void tiny_eval(const DatasetView& ds, const ProjView& pv, int64_t q, bool have,
-                                          int sid, int yv, int nv, const int* N, int lane, TinyEval& te) {
-  const int rb = pv.beg[q];
-  int k = pv.end[q] - rb;
-  k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
-  int fl = 0, sl = 1;
-  if (lane < k) {
-    fl = pv.feat[rb + lane];
-    fl = (fl < 0 || fl >= ds.d) ? 0 : fl;
-    sl = pv.sign[rb + lane];
-  }
-  float v = 0.0f;
-  for (int jj = 0; jj < k; ++jj) {
-    const int f = __shfl_sync(0xffffffffu, fl, jj);
-    const int sg = __shfl_sync(0xffffffffu, sl, jj);
-    const float x = have ? __ldg(ds.X + (int64_t)f * ds.ld + sid) : 0.0f;
-    v = __fadd_rn(v, sg == 1 ? x : -x);
-  }
-  unsigned long long val = have ? sort_key(v, yv) : ~0ull;
-  val = warp_bitonic32(val, lane);
-  te.val = val;
-  const int ys = (int)(val & 0xFFull);
-  const unsigned key = (unsigned)(val >> 32);
-  const unsigned nxt = __shfl_down_sync(0xffffffffu, key, 1);
-  const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
-  const bool valid = lane < nv;
-  int nL = lane + 1;
-#pragma unroll
-  for (int c = 0; c < kMaxClasses; ++c) {
-    const unsigned bal = __ballot_sync(0xffffffffu, valid && ys == c);
-    te.L[c] = __popc(bal & le);
-  }
-  te.cand = (lane < nv - 1) && (key != nxt);
-  te.g32 = te.cand ? gain32(te.L, N, ds.C, nv, nL) : -1.0f;
-}
-
-__global__ void __launch_bounds__(256) k_sort_tiny(DatasetView ds, const int32_t* __restrict__ idx,
-                                                   const int64_t* __restrict__ off, ProjView pv,
-                                                   const V4* plan_total, const int32_t* tiny_nodes, float eps,
-                                                   so_split* out, int64_t* left_counts) {
-  extern __shared__ float s_m32_all[];  // [8 warps][P]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* s_m32 = s_m32_all + warp * pv.P;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t m_tiny = plan_total->y;
-  const int C = ds.C, P = pv.P;
-  for (int64_t s = gw; s < m_tiny; s += nw) {
-    const int j = tiny_nodes[s];
-    const int64_t beg = off[j];
-    const int nv = (int)(off[j + 1] - beg);
-    const bool have = lane < nv;
-    const int sid = have ? (int)safe_sample(idx[beg + lane], ds.n) : 0;
-    const int yv = have ? ds.y[sid] : 0;
-    int N[kMaxClasses];
-#pragma unroll
-    for (int c = 0; c < kMaxClasses; ++c) N[c] = __popc(__ballot_sync(0xffffffffu, have && yv == c));
-    float M = -1.0f;
-    TinyEval te;
-    for (int p = 0; p < P; ++p) {
-      tiny_eval(ds, pv, (int64_t)j * P + p, have, sid, yv, nv, N, lane, te);
-      const float mp = warp_max(te.g32);
-      if (lane == 0) s_m32[p] = mp;
-      M = fmaxf(M, mp);
-    }
-    __syncwarp();
-    so_split r;
-    r.path = 1;
-    if (!(M > 0.0f)) {
-      if (lane == 0) {
-        r.valid = 0; r.proj = -1; r.cand = -1; r.threshold = 0.0f; r.gain = 0.0; r.n_left = 0; r.n_right = 0;
-        out[j] = r;
-        if (left_counts)
-          for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = 0;
-      }
-      continue;
-    }
-    const float thr = __fmul_rn(M, 1.0f - eps);
-    Cand best{-1.0, INT_MAX, INT_MAX};
-    for (int p = 0; p < P; ++p) {
-      if (s_m32[p] < thr) continue;
-      tiny_eval(ds, pv, (int64_t)j * P + p, have, sid, yv, nv, N, lane, te);
-      Cand c{-1.0, INT_MAX, INT_MAX};
-      if (te.cand && te.g32 >= thr) c = Cand{gain64(te.L, N, C, nv, lane + 1), p, lane};
-      c = warp_best(c);
-      if (better(c, best)) best = c;
-    }
-    if (best.proj == INT_MAX) {  // cannot happen: the float maximum is always re-scored
-      if (lane == 0) {
-        r.valid = 0; r.proj = -1; r.cand = -1; r.threshold = 0.0f; r.gain = 0.0; r.n_left = 0; r.n_right = 0;
-        out[j] = r;
-      }
-      continue;
-    }
-    // final: re-evaluate the winner for its threshold and left counts
-    tiny_eval(ds, pv, (int64_t)j * P + best.proj, have, sid, yv, nv, N, lane, te);
-    const unsigned key = (unsigned)(te.val >> 32);
-    const unsigned nxt = __shfl_down_sync(0xffffffffu, key, 1);
-    int Lw[kMaxClasses];
-#pragma unroll
-    for (int c = 0; c < kMaxClasses; ++c) Lw[c] = __shfl_sync(0xffffffffu, te.L[c], best.cand);
-    const unsigned ka = __shfl_sync(0xffffffffu, key, best.cand);
-    const unsigned kb = __shfl_sync(0xffffffffu, nxt, best.cand);
-    if (lane == 0) {
-      r.valid = 1;
-      r.proj = best.proj;
-      r.cand = best.cand;
-      r.threshold = midpoint(key2f(ka), key2f(kb));
-      r.gain = best.g;
-      r.n_left = best.cand + 1;
-      r.n_right = nv - (best.cand + 1);
-      out[j] = r;
-      if (left_counts)
-        for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = Lw[c];
-    }
-    __syncwarp();
-  }
-}
-
-// Medium nodes (33 .. T-1 samples): one CTA (8 warps) per node, one warp per
-// projection, bitonic sort of the projection's (value, label) keys in the
-// warp's shared buffer.
-constexpr int kMedWarps = 8;
-
-struct MedShared {
-  int32_t* sidx;   // [T]
-  uint8_t* sy;     // [T]
-  float* m32;      // [P]
-  unsigned long long* buf;  // [kMedWarps][NP]
-};
-
-__device__ __forceinline__ void med_sort_eval(const DatasetView& ds, const ProjView& pv, int64_t q,
-                                              const int32_t* sidx, const uint8_t* sy, int nv, int NP,
-                                              unsigned long long* buf, int lane) {
-  __shared__ int32_t s_f[kMedWarps][kMaxCap];
-  __shared__ int8_t s_s[kMedWarps][kMaxCap];
-  const int warp = threadIdx.x >> 5;
-  __syncwarp();
-  const int k = load_row(pv, q, ds.d, s_f[warp], s_s[warp], lane);
-  for (int e = lane; e < NP; e += 32) {
-    unsigned long long val = ~0ull;
-    if (e < nv) val = sort_key(project_value(ds.X, ds.ld, sidx[e], s_f[warp], s_s[warp], k), sy[e]);
-    buf[e] = val;
-  }
-  __syncwarp();
-  for (int kk = 2; kk <= NP; kk <<= 1) {
-    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-      for (int i = lane; i < NP / 2; i += 32) {
-        const int lo = ((i & ~(jj - 1)) << 1) | (i & (jj - 1));
-        const int hi = lo + jj;
-        const bool up = (lo & kk) == 0;
-        const unsigned long long a = buf[lo], b = buf[hi];
-        if ((a > b) == up) {
-          buf[lo] = b;
-          buf[hi] = a;
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
-// Walks the sorted buffer: lane owns positions [lane*E, lane*E+E).  Calls
-// visit(i, L, g32) for every candidate i (boundary between distinct values).
-template <class Visit>
-__device__ __forceinline__ void med_scan(const unsigned long long* buf, int nv, int NP, const int* N, int C,
-                                         int lane, Visit visit) {
-  const int E = NP / 32;
-  const int i0 = lane * E;
-  Packed own{0, 0};
-  for (int e = 0; e < E; ++e) {
-    const int i = i0 + e;
-    if (i < nv) packed_add(own, (int)(buf[i] & 0xFFull));
-  }
-  // exclusive warp scan of the packed counters (fields never overflow: nv < 65536)
-  unsigned long long ilo = own.lo, ihi = own.hi;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long ul = __shfl_up_sync(0xffffffffu, ilo, o);
-    const unsigned long long uh = __shfl_up_sync(0xffffffffu, ihi, o);
-    if (lane >= o) {
-      ilo += ul;
-      ihi += uh;
-    }
-  }
-  Packed run{ilo - own.lo, ihi - own.hi};
-  for (int e = 0; e < E; ++e) {
-    const int i = i0 + e;
-    if (i >= nv - 1) break;
-    const unsigned long long a = buf[i];
-    packed_add(run, (int)(a & 0xFFull));
-    const unsigned long long b = buf[i + 1];
-    if ((unsigned)(a >> 32) != (unsigned)(b >> 32)) {
-      int L[kMaxClasses];
-#pragma unroll
-      for (int c = 0; c < kMaxClasses; ++c) L[c] = packed_get(run, c);
-      visit(i, L, gain32(L, N, C, nv, i + 1));
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kMedWarps * 32) k_sort_medium(DatasetView ds, const int32_t* __restrict__ idx,
-                                                               const int64_t* __restrict__ off, ProjView pv,
-                                                               const V4* plan_total, const int32_t* med_nodes,
-                                                               int32_t T, int32_t NPmax, float eps, so_split* out,
-                                                               int64_t* left_counts) {
-  extern __shared__ unsigned long long s_dyn[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int P = pv.P, C = ds.C;
-  unsigned long long* buf = s_dyn + (int64_t)warp * NPmax;
-  int32_t* sidx = reinterpret_cast<int32_t*>(s_dyn + (int64_t)kMedWarps * NPmax);
-  float* m32 = reinterpret_cast<float*>(sidx + T);
-  uint8_t* sy = reinterpret_cast<uint8_t*>(m32 + P);
-  __shared__ int s_N[kMaxClasses];
-  __shared__ float s_red[kMedWarps];
-  __shared__ Cand s_best[kMedWarps];
-  const int64_t m_med = plan_total->w;
-  for (int64_t s = blockIdx.x; s < m_med; s += gridDim.x) {
-    const int j = med_nodes[s];
-    const int64_t beg = off[j];
-    const int nv = (int)(off[j + 1] - beg);
-    int NP = 32;
-    while (NP < nv) NP <<= 1;
-    if (threadIdx.x < kMaxClasses) s_N[threadIdx.x] = 0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < nv; e += blockDim.x) {
-      const int32_t sid = (int32_t)safe_sample(idx[beg + e], ds.n);
-      sidx[e] = sid;
-      const int yv = ds.y[sid];
-      sy[e] = (uint8_t)yv;
-      if (yv < C) atomicAdd(&s_N[yv], 1);
-    }
-    __syncthreads();
-    int N[kMaxClasses];
-#pragma unroll
-    for (int c = 0; c < kMaxClasses; ++c) N[c] = s_N[c];
-    // sweep 1: float maximum of every projection
-    for (int p = warp; p < P; p += kMedWarps) {
-      med_sort_eval(ds, pv, (int64_t)j * P + p, sidx, sy, nv, NP, buf, lane);
-      float mp = -1.0f;
-      med_scan(buf, nv, NP, N, C, lane, [&](int, const int*, float g) { mp = fmaxf(mp, g); });
-      mp = warp_max(mp);
-      if (lane == 0) m32[p] = mp;
-    }
-    __syncthreads();
-    float m = -1.0f;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) m = fmaxf(m, m32[p]);
-    m = warp_max(m);
-    if (lane == 0) s_red[warp] = m;
-    __syncthreads();
-    float M = s_red[0];
-    for (int w = 1; w < kMedWarps; ++w) M = fmaxf(M, s_red[w]);
-    if (!(M > 0.0f)) {
-      if (threadIdx.x == 0) {
-        so_split r;
-        r.valid = 0; r.proj = -1; r.path = 1; r.cand = -1; r.threshold = 0.0f; r.gain = 0.0;
-        r.n_left = 0; r.n_right = 0;
-        out[j] = r;
-        if (left_counts)
-          for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = 0;
-      }
-      __syncthreads();
-      continue;
-    }
-    const float thr = __fmul_rn(M, 1.0f - eps);
-    // sweep 2: double re-score of the near-ties
-    Cand best{-1.0, INT_MAX, INT_MAX};
-    for (int p = warp; p < P; p += kMedWarps) {
-      if (m32[p] < thr) continue;
-      med_sort_eval(ds, pv, (int64_t)j * P + p, sidx, sy, nv, NP, buf, lane);
-      Cand lb{-1.0, INT_MAX, INT_MAX};
-      med_scan(buf, nv, NP, N, C, lane, [&](int i, const int* L, float g) {
-        if (g >= thr) {
-          const Cand c{gain64(L, N, C, nv, i + 1), p, i};
-          if (better(c, lb)) lb = c;
-        }
-      });
-      lb = warp_best(lb);
-      if (better(lb, best)) best = lb;
-    }
-    if (lane == 0) s_best[warp] = best;
-    __syncthreads();
-    Cand f = s_best[0];
-    for (int w = 1; w < kMedWarps; ++w)
-      if (better(s_best[w], f)) f = s_best[w];
-    // warp 0 recomputes the winner for its threshold and left counts
-    if (warp == 0 && f.proj != INT_MAX) {
-      med_sort_eval(ds, pv, (int64_t)j * P + f.proj, sidx, sy, nv, NP, buf, lane);
-      if (lane == 0) {
-        int Lc[kMaxClasses];
-        for (int c = 0; c < kMaxClasses; ++c) Lc[c] = 0;
-        for (int i = 0; i <= f.cand; ++i) Lc[(int)(buf[i] & 0xFFull)]++;
-        const float a = key2f((unsigned)(buf[f.cand] >> 32));
-        const float b = key2f((unsigned)(buf[f.cand + 1] >> 32));
-        so_split r;
-        r.valid = 1;
-        r.proj = f.proj;
-        r.path = 1;
-        r.cand = f.cand;
-        r.threshold = midpoint(a, b);
-        r.gain = f.g;
-        r.n_left = f.cand + 1;
-        r.n_right = nv - (f.cand + 1);
-        out[j] = r;
-        if (left_counts)
-          for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = Lc[c];
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// ============================================================================
 // Search driver
 // ============================================================================
 void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int32_t P, int32_t C,
@@ -861,6 +504,8 @@ void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int3
   s.sort_nodes = cv.take<int32_t>(2 * (size_t)m + 2);
   s.item_off = cv.take<int64_t>((size_t)m + 1);
   s.err = cv.take<int32_t>((size_t)m + 1);  // per-node bad-row flags
+  s.sort_res = cv.take<unsigned char>((size_t)m * P * sort_res_bytes());
+  s.node_cls = cv.take<int32_t>((size_t)m * kMaxClasses);
   s.mm_keys = cv.take<uint32_t>((size_t)mh * P * 2);
   s.max32 = cv.take<float>((size_t)mh * P);
   s.node_counts = cv.take<int32_t>((size_t)mh * C);
@@ -948,32 +593,8 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
                                              s.mm_keys, a.eps, a.out, a.left_counts);
   }
   // exact path
-  {
-    const size_t smem_t = (size_t)8 * P * sizeof(float);
-    if (smem_t > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_sort_tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-      if (e != cudaSuccess) return e;
-    }
-    {
-      ProfScope ps_("k_sort_tiny", st);
-      k_sort_tiny<<<grid_fill, 256, smem_t, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.sort_nodes, a.eps,
-                                                  a.out, a.left_counts);
-    }
-  }
-  if (!a.hist_only && a.T > 33) {
-    int NPmax = 32;
-    while (NPmax < a.T - 1) NPmax <<= 1;
-    const size_t smem = (size_t)kMedWarps * NPmax * 8 + (size_t)a.T * 4 + (size_t)P * 4 + (size_t)a.T + 16;
-    e = cudaFuncSetAttribute(k_sort_medium, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int occ = occupancy(k_sort_medium, kMedWarps * 32, smem);
-    {
-      ProfScope ps_("k_sort_medium", st);
-      k_sort_medium<<<di.num_sms * occ, kMedWarps * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
-                                                                    s.sort_nodes + a.m + 1, a.T, NPmax, a.eps,
-                                                                    a.out, a.left_counts);
-    }
-  }
+  e = launch_sort_warp(a, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls, st);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1117,7 +738,7 @@ cudaError_t launch_sample(int32_t m, const uint64_t* keys, int32_t P, int32_t d,
 // Stable partition (batched over the frontier)
 // ============================================================================
 constexpr int kPartThreads = 256;
-constexpr int kPartPer = 16;
+constexpr int kPartPer = 4;
 constexpr int kPartTile = kPartThreads * kPartPer;
 
 int64_t part_tiles(int64_t n) { return (n + kPartTile - 1) / kPartTile; }

@@ -121,7 +121,7 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   a.hist_only = params->hist_only ? 1 : 0;
   {
     // same re-score window rule as the allocating entry points
-    const float floor_eps = 2.5f * (float)(C + 6) * 5.9604645e-8f;
+    const float floor_eps = 3.5f * (float)(C + 6) * 5.9604645e-8f;
     float eps = params->rescore_rel_eps > 0.0f ? params->rescore_rel_eps : 4e-6f;
     a.eps = eps < floor_eps ? floor_eps : eps;
   }

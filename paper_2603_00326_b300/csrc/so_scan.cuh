@@ -10,7 +10,7 @@
 namespace sof {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanPer = 8;
+constexpr int kScanPer = 2;
 constexpr int kScanTile = kScanThreads * kScanPer;
 
 __device__ __forceinline__ V4 v4add(const V4& a, const V4& b) {

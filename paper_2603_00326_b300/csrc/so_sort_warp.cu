@@ -1,0 +1,528 @@
+// so_sort_warp.cu -- exact path (Section 3.1: small nodes are split exactly by
+// sorting): one warp per (node, projection).
+//
+// Pass 1: the warp gathers the node's projected values and sorts the
+// (order-preserving key, label) pairs -- in registers for nodes of up to 512
+// samples (bitonic network, lane-major layout e = lane*EPL + r), in the
+// warp's shared-memory buffer for 513..2047 samples -- forms class prefix
+// counts with a packed warp scan, evaluates the float Gini gain of every
+// boundary between distinct values, takes the projection's float maximum
+// M_p, re-scores in double every candidate within M_p(1-eps) and stores the
+// projection's lexicographic best (double gain, lowest position).
+// Pass 2 (k_sortw_select): one warp per node takes M = max_p M_p and the
+// lexicographic best (gain, projection, position) over the projections with
+// M_p >= M(1-eps).  The double winner of the node is always in its
+// projection's re-score set (M >= M_p), and every projection holding a
+// double tie of it has M_p >= M(1-eps) when eps exceeds three times the float
+// gain's relative error, so the result equals the double argmax.
+#include <climits>
+
+#include "so_device.cuh"
+#include "so_internal.h"
+
+namespace sof {
+
+namespace {
+
+struct PackedCnt {
+  unsigned long long lo, hi;  // 16-bit class counters: classes 0-3 in lo, 4-7 in hi
+};
+__device__ __forceinline__ void pc_add(PackedCnt& a, int y) {
+  if (y < 4) a.lo += 1ull << (16 * y);
+  else if (y < kMaxClasses) a.hi += 1ull << (16 * (y - 4));
+}
+__device__ __forceinline__ int pc_get(const PackedCnt& a, int c) {
+  return (int)(((c < 4) ? (a.lo >> (16 * c)) : (a.hi >> (16 * (c - 4)))) & 0xFFFFull);
+}
+
+template <int EPL>
+__device__ __forceinline__ void cmpswap(unsigned long long (&k)[EPL], int r, int rp, bool up) {
+  const unsigned long long a = k[r], b = k[rp];
+  const bool sw = (a > b) == up;
+  k[r] = sw ? b : a;
+  k[rp] = sw ? a : b;
+}
+
+// Bitonic sort of 32*EPL keys, element e = lane*EPL + r, ascending.
+template <int EPL>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&k)[EPL], int lane) {
+  constexpr int NP = 32 * EPL;
+#pragma unroll
+  for (int size = 2; size <= NP; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < EPL) {
+#pragma unroll
+        for (int r = 0; r < EPL; ++r) {
+          const int rp = r ^ stride;
+          if (rp > r) {
+            const int e = lane * EPL + r;
+            cmpswap<EPL>(k, r, rp, (e & size) == 0);
+          }
+        }
+      } else {
+        const int ls = stride / EPL;
+        const bool lower = (lane & ls) == 0;
+#pragma unroll
+        for (int r = 0; r < EPL; ++r) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, k[r], ls);
+          const int e = lane * EPL + r;
+          const bool up = (e & size) == 0;
+          const unsigned long long mn = k[r] < o ? k[r] : o;
+          const unsigned long long mx = k[r] < o ? o : k[r];
+          k[r] = (lower == up) ? mn : mx;
+        }
+      }
+    }
+  }
+}
+
+struct SortNodeCtx {
+  int64_t beg;
+  int nv;
+  int N[kMaxClasses];
+};
+
+// Loads, projects and sorts one projection of one node; returns the lane's
+// keys in k[] (padding keys are all-ones and sort last).
+template <int EPL>
+__device__ __forceinline__ void load_sort(const DatasetView& ds, const int32_t* __restrict__ idx, const ProjView& pv,
+                                          int64_t q, const SortNodeCtx& nc, int lane, unsigned long long (&k)[EPL]) {
+  const int rb = pv.beg[q];
+  int kk = pv.end[q] - rb;
+  kk = kk < 0 ? 0 : (kk > kMaxCap ? kMaxCap : kk);
+  int fl = 0, sl = 1;
+  if (lane < kk) {
+    fl = pv.feat[rb + lane];
+    fl = (fl < 0 || fl >= ds.d) ? 0 : fl;
+    sl = pv.sign[rb + lane];
+  }
+  int32_t sid[EPL];
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) {
+    const int e = lane * EPL + r;
+    sid[r] = e < nc.nv ? (int32_t)safe_sample(idx[nc.beg + e], ds.n) : -1;
+  }
+  float v[EPL];
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) v[r] = 0.0f;
+  for (int jj = 0; jj < kk; ++jj) {
+    const int f = __shfl_sync(0xffffffffu, fl, jj);
+    const int sg = __shfl_sync(0xffffffffu, sl, jj);
+    const float* col = ds.X + (int64_t)f * ds.ld;
+#pragma unroll
+    for (int r = 0; r < EPL; ++r) {
+      if (sid[r] >= 0) {
+        const float x = __ldg(col + sid[r]);
+        v[r] = __fadd_rn(v[r], sg == 1 ? x : -x);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) {
+    if (sid[r] >= 0) {
+      const int yv = ds.y[sid[r]];
+      k[r] = ((unsigned long long)f2key(v[r]) << 32) | (unsigned long long)(unsigned)yv;
+    } else {
+      k[r] = ~0ull;
+    }
+  }
+  warp_bitonic<EPL>(k, lane);
+}
+
+// Walks the sorted keys; calls visit(e, run, g32, a, b) for every candidate e
+// (a boundary between distinct values a < b), run = packed class counts of
+// positions 0..e.
+template <int EPL, class Visit>
+__device__ __forceinline__ void scan_candidates(const unsigned long long (&k)[EPL], const SortNodeCtx& nc, int C,
+                                                int lane, Visit visit) {
+  PackedCnt own{0, 0};
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) {
+    const int e = lane * EPL + r;
+    if (e < nc.nv) pc_add(own, (int)(k[r] & 0xFFull));
+  }
+  unsigned long long ilo = own.lo, ihi = own.hi;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long ul = __shfl_up_sync(0xffffffffu, ilo, o);
+    const unsigned long long uh = __shfl_up_sync(0xffffffffu, ihi, o);
+    if (lane >= o) {
+      ilo += ul;
+      ihi += uh;
+    }
+  }
+  PackedCnt run{ilo - own.lo, ihi - own.hi};
+  // the key right after this lane's last element: the next lane's first
+  const unsigned next_first = (unsigned)(__shfl_down_sync(0xffffffffu, k[0], 1) >> 32);
+#pragma unroll
+  for (int r = 0; r < EPL; ++r) {
+    const int e = lane * EPL + r;
+    if (e < nc.nv) pc_add(run, (int)(k[r] & 0xFFull));
+    if (e < nc.nv - 1) {
+      const unsigned a = (unsigned)(k[r] >> 32);
+      const unsigned b = (r + 1 < EPL) ? (unsigned)(k[(r + 1) < EPL ? r + 1 : r] >> 32) : next_first;
+      if (a != b) {
+        int L[kMaxClasses];
+#pragma unroll
+        for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
+        visit(e, run, gain32(L, nc.N, C, nc.nv, e + 1), a, b);
+      }
+    }
+  }
+}
+
+// Node context from its offsets and the class counts computed once per node.
+__device__ __forceinline__ void node_ctx(const int64_t* off, const int32_t* nodes, int64_t s,
+                                         const int32_t* __restrict__ node_cls, SortNodeCtx& nc, int& j) {
+  j = nodes[s];
+  nc.beg = off[j];
+  nc.nv = (int)(off[j + 1] - nc.beg);
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) nc.N[c] = node_cls[(int64_t)j * kMaxClasses + c];
+}
+
+// Per-(node, projection) result of pass 1.
+struct SortRes {
+  double g64;             // best double gain of the projection (-1: none)
+  float m32;              // float maximum of the projection (-1: no candidate)
+  int cand;               // sorted position of the best candidate
+  unsigned ka, kb;        // keys of the values around the boundary
+  unsigned long long llo, lhi;  // packed left class counts
+};
+
+struct Best {
+  Cand c;
+  unsigned ka, kb;
+  PackedCnt L;  // class counts of the left side
+};
+
+__device__ __forceinline__ void best_reduce(Best& lb) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Best other;
+    other.c.g = __shfl_xor_sync(0xffffffffu, lb.c.g, o);
+    other.c.proj = __shfl_xor_sync(0xffffffffu, lb.c.proj, o);
+    other.c.cand = __shfl_xor_sync(0xffffffffu, lb.c.cand, o);
+    other.ka = __shfl_xor_sync(0xffffffffu, lb.ka, o);
+    other.kb = __shfl_xor_sync(0xffffffffu, lb.kb, o);
+    other.L.lo = __shfl_xor_sync(0xffffffffu, lb.L.lo, o);
+    other.L.hi = __shfl_xor_sync(0xffffffffu, lb.L.hi, o);
+    if (better(other.c, lb.c)) lb = other;
+  }
+}
+
+// Both sweeps of pass 1 over an already sorted projection, through a
+// candidate walker walk(visit); writes the projection's SortRes.
+template <class Walk>
+__device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, float eps, int lane, Walk walk,
+                                                 SortRes* out) {
+  float m = -1.0f;
+  walk([&](int, const PackedCnt&, float g, unsigned, unsigned) { m = fmaxf(m, g); });
+  m = warp_max(m);
+  Best lb;
+  lb.c = Cand{-1.0, INT_MAX, INT_MAX};
+  lb.ka = lb.kb = 0u;
+  lb.L = PackedCnt{0, 0};
+  if (m > 0.0f) {
+    const float thr = __fmul_rn(m, 1.0f - eps);
+    walk([&](int e, const PackedCnt& run, float g, unsigned a, unsigned b) {
+      if (g >= thr) {
+        int L[kMaxClasses];
+#pragma unroll
+        for (int cc = 0; cc < kMaxClasses; ++cc) L[cc] = pc_get(run, cc);
+        const Cand c{gain64(L, nc.N, C, nc.nv, e + 1), 0, e};
+        if (better(c, lb.c)) {
+          lb.c = c;
+          lb.ka = a;
+          lb.kb = b;
+          lb.L = run;
+        }
+      }
+    });
+    best_reduce(lb);
+  }
+  if (lane == 0) {
+    SortRes r;
+    r.m32 = m;
+    r.g64 = lb.c.g;
+    r.cand = lb.c.cand;
+    r.ka = lb.ka;
+    r.kb = lb.kb;
+    r.llo = lb.L.lo;
+    r.lhi = lb.L.hi;
+    *out = r;
+  }
+}
+
+template <int EPL>
+__device__ __forceinline__ void proj_pass1_reg(const DatasetView& ds, const int32_t* idx, const ProjView& pv, int64_t q,
+                                               const SortNodeCtx& nc, int lane, float eps, SortRes* out) {
+  unsigned long long k[EPL];
+  load_sort<EPL>(ds, idx, pv, q, nc, lane, k);
+  score_projection(nc, ds.C, eps, lane, [&](auto visit) { scan_candidates<EPL>(k, nc, ds.C, lane, visit); }, out);
+}
+
+// Shared-memory form for 513..2047 samples: the warp's buffer holds NP keys.
+__device__ __forceinline__ void proj_pass1_smem(const DatasetView& ds, const int32_t* idx, const ProjView& pv,
+                                                int64_t q, const SortNodeCtx& nc, int lane, float eps,
+                                                unsigned long long* buf, SortRes* out) {
+  int NP = 1024;
+  while (NP < nc.nv) NP <<= 1;
+  const int rb = pv.beg[q];
+  int kk = pv.end[q] - rb;
+  kk = kk < 0 ? 0 : (kk > kMaxCap ? kMaxCap : kk);
+  int fl = 0, sl = 1;
+  if (lane < kk) {
+    fl = pv.feat[rb + lane];
+    fl = (fl < 0 || fl >= ds.d) ? 0 : fl;
+    sl = pv.sign[rb + lane];
+  }
+  for (int e0 = 0; e0 < NP; e0 += 32) {
+    // all lanes take part (the shuffles need a converged warp); positions
+    // past the node compute on its first sample and store a padding key
+    const int e = e0 + lane;
+    const bool live = e < nc.nv;
+    const int64_t sid = safe_sample(idx[nc.beg + (live ? e : 0)], ds.n);
+    float v = 0.0f;
+    for (int jj = 0; jj < kk; ++jj) {
+      const int f = __shfl_sync(0xffffffffu, fl, jj);
+      const int sg = __shfl_sync(0xffffffffu, sl, jj);
+      const float x = __ldg(ds.X + (int64_t)f * ds.ld + sid);
+      v = __fadd_rn(v, sg == 1 ? x : -x);
+    }
+    buf[e] = live ? (((unsigned long long)f2key(v) << 32) | (unsigned long long)(unsigned)ds.y[sid]) : ~0ull;
+  }
+  __syncwarp();
+  for (int size = 2; size <= NP; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = lane; i < NP / 2; i += 32) {
+        const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const unsigned long long a = buf[lo], b = buf[hi];
+        if ((a > b) == up) {
+          buf[lo] = b;
+          buf[hi] = a;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // lane owns positions [lane*E, lane*E + E)
+  const int E = NP / 32;
+  const int i0 = lane * E;
+  auto walk = [&](auto visit) {
+    PackedCnt own{0, 0};
+    for (int e = 0; e < E; ++e)
+      if (i0 + e < nc.nv) pc_add(own, (int)(buf[i0 + e] & 0xFFull));
+    unsigned long long ilo = own.lo, ihi = own.hi;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long ul = __shfl_up_sync(0xffffffffu, ilo, o);
+      const unsigned long long uh = __shfl_up_sync(0xffffffffu, ihi, o);
+      if (lane >= o) {
+        ilo += ul;
+        ihi += uh;
+      }
+    }
+    PackedCnt run{ilo - own.lo, ihi - own.hi};
+    for (int e = 0; e < E; ++e) {
+      const int i = i0 + e;
+      if (i >= nc.nv - 1) break;
+      const unsigned long long x = buf[i];
+      pc_add(run, (int)(x & 0xFFull));
+      const unsigned a = (unsigned)(x >> 32), b = (unsigned)(buf[i + 1] >> 32);
+      if (a != b) {
+        int L[kMaxClasses];
+#pragma unroll
+        for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
+        visit(i, run, gain32(L, nc.N, ds.C, nc.nv, i + 1), a, b);
+      }
+    }
+  };
+  score_projection(nc, ds.C, eps, lane, walk, out);
+  __syncwarp();
+}
+
+__device__ __forceinline__ int epl_of(int nv) {
+  return nv <= 32 ? 1 : nv <= 64 ? 2 : nv <= 128 ? 4 : nv <= 256 ? 8 : 16;
+}
+
+}  // namespace
+
+// Pass 1, register form: one warp per (node of <= 512 samples, projection).
+__global__ void __launch_bounds__(256, 2) k_sortw_scan(DatasetView ds, const int32_t* __restrict__ idx,
+                                                       const int64_t* __restrict__ off, ProjView pv,
+                                                       const V4* plan_total, const int32_t* nodes,
+                                                       const int32_t* __restrict__ node_cls, float eps,
+                                                       SortRes* res) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int P = pv.P;
+  const int64_t total = plan_total->y * P;
+  for (int64_t t = gw; t < total; t += nw) {
+    const int64_t s = t / P;
+    const int p = (int)(t - s * P);
+    SortNodeCtx nc;
+    int j;
+    node_ctx(off, nodes, s, node_cls, nc, j);
+    const int64_t q = (int64_t)j * P + p;
+    SortRes* out = res + q;
+    switch (epl_of(nc.nv)) {
+      case 1: proj_pass1_reg<1>(ds, idx, pv, q, nc, lane, eps, out); break;
+      case 2: proj_pass1_reg<2>(ds, idx, pv, q, nc, lane, eps, out); break;
+      case 4: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, eps, out); break;
+      case 8: proj_pass1_reg<8>(ds, idx, pv, q, nc, lane, eps, out); break;
+      default: proj_pass1_reg<16>(ds, idx, pv, q, nc, lane, eps, out); break;
+    }
+  }
+}
+
+// Pass 1, shared-memory form: one warp per (node of 513..2047 samples, projection).
+constexpr int kSwSmemWarps = 4;
+__global__ void __launch_bounds__(kSwSmemWarps * 32) k_sortw_scan_smem(DatasetView ds, const int32_t* __restrict__ idx,
+                                                                      const int64_t* __restrict__ off, ProjView pv,
+                                                                      const V4* plan_total, const int32_t* nodes,
+                                                                      const int32_t* __restrict__ node_cls,
+                                                                      int NPmax, float eps, SortRes* res) {
+  extern __shared__ unsigned long long s_keys[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long* buf = s_keys + (int64_t)warp * NPmax;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int P = pv.P;
+  const int64_t total = plan_total->w * P;
+  for (int64_t t = gw; t < total; t += nw) {
+    const int64_t s = t / P;
+    const int p = (int)(t - s * P);
+    SortNodeCtx nc;
+    int j;
+    node_ctx(off, nodes, s, node_cls, nc, j);
+    const int64_t q = (int64_t)j * P + p;
+    proj_pass1_smem(ds, idx, pv, q, nc, lane, eps, buf, res + q);
+  }
+}
+
+// Class counts of every exact-path node (one warp per node).
+__global__ void __launch_bounds__(256) k_sortw_counts(DatasetView ds, const int32_t* __restrict__ idx,
+                                                      const int64_t* __restrict__ off, const V4* plan_total,
+                                                      const int32_t* tiny, const int32_t* med, int32_t* node_cls) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t m_tiny = plan_total->y, m_all = plan_total->y + plan_total->w;
+  for (int64_t s = gw; s < m_all; s += nw) {
+    const int j = s < m_tiny ? tiny[s] : med[s - m_tiny];
+    const int64_t beg = off[j];
+    const int nv = (int)(off[j + 1] - beg);
+    int cnt[kMaxClasses];
+#pragma unroll
+    for (int c = 0; c < kMaxClasses; ++c) cnt[c] = 0;
+    for (int e = lane; e < nv; e += 32) {
+      const int yv = ds.y[safe_sample(idx[beg + e], ds.n)];
+#pragma unroll
+      for (int c = 0; c < kMaxClasses; ++c) cnt[c] += (yv == c);
+    }
+#pragma unroll
+    for (int c = 0; c < kMaxClasses; ++c) {
+      const int v = warp_sum(cnt[c]);
+      if (lane == c) node_cls[(int64_t)j * kMaxClasses + c] = v;
+    }
+  }
+}
+
+// Pass 2: one warp per exact-path node (both forms).
+__global__ void __launch_bounds__(256) k_sortw_select(const int64_t* __restrict__ off, int32_t P, int32_t C,
+                                                      const V4* plan_total, const int32_t* tiny, const int32_t* med,
+                                                      const SortRes* __restrict__ res, float eps, so_split* out,
+                                                      int64_t* left_counts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t m_tiny = plan_total->y, m_all = plan_total->y + plan_total->w;
+  for (int64_t s = gw; s < m_all; s += nw) {
+    const int j = s < m_tiny ? tiny[s] : med[s - m_tiny];
+    const int nv = (int)(off[j + 1] - off[j]);
+    const SortRes* rj = res + (int64_t)j * P;
+    float M = -1.0f;
+    for (int p = lane; p < P; p += 32) M = fmaxf(M, rj[p].m32);
+    M = warp_max(M);
+    Cand best{-1.0, INT_MAX, INT_MAX};
+    if (M > 0.0f) {
+      const float thr = __fmul_rn(M, 1.0f - eps);
+      for (int p = lane; p < P; p += 32) {
+        const SortRes r = rj[p];
+        if (r.m32 >= thr && r.g64 >= 0.0) {
+          const Cand c{r.g64, p, r.cand};
+          if (better(c, best)) best = c;
+        }
+      }
+      best = warp_best(best);
+    }
+    if (lane == 0) {
+      so_split rec;
+      rec.path = 1;
+      if (best.proj == INT_MAX) {
+        rec.valid = 0; rec.proj = -1; rec.cand = -1; rec.threshold = 0.0f; rec.gain = 0.0;
+        rec.n_left = 0; rec.n_right = 0;
+        out[j] = rec;
+        if (left_counts)
+          for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = 0;
+      } else {
+        const SortRes r = rj[best.proj];
+        rec.valid = 1;
+        rec.proj = best.proj;
+        rec.cand = r.cand;
+        rec.threshold = midpoint(key2f(r.ka), key2f(r.kb));
+        rec.gain = r.g64;
+        rec.n_left = r.cand + 1;
+        rec.n_right = nv - (r.cand + 1);
+        out[j] = rec;
+        if (left_counts) {
+          const PackedCnt L{r.llo, r.lhi};
+          for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = pc_get(L, c);
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_sort_warp(const SearchArgs& a, const V4* plan_total, const int32_t* tiny, const int32_t* med,
+                             void* res_raw, int32_t* node_cls, cudaStream_t st) {
+  const DeviceInfo& di = device_info();
+  SortRes* res = static_cast<SortRes*>(res_raw);
+  {
+    ProfScope ps_("k_sortw_counts", st);
+    k_sortw_counts<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, plan_total, tiny, med, node_cls);
+  }
+  {
+    ProfScope ps_("k_sortw_scan", st);
+    k_sortw_scan<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, tiny, node_cls, a.eps,
+                                                 res);
+  }
+  if (!a.hist_only && a.T > 513) {
+    int NPmax = 1024;
+    while (NPmax < a.T - 1) NPmax <<= 1;
+    const size_t smem = (size_t)kSwSmemWarps * NPmax * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_sortw_scan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sortw_scan_smem, kSwSmemWarps * 32, smem);
+    if (occ < 1) occ = 1;
+    ProfScope ps_("k_sortw_scan_smem", st);
+    k_sortw_scan_smem<<<di.num_sms * occ, kSwSmemWarps * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total,
+                                                                         med, node_cls, NPmax, a.eps, res);
+  }
+  {
+    ProfScope ps_("k_sortw_select", st);
+    k_sortw_select<<<di.num_sms * 8, 256, 0, st>>>(a.node_off, a.pv.P, a.ds.C, plan_total, tiny, med, res, a.eps,
+                                                   a.out, a.left_counts);
+  }
+  return cudaGetLastError();
+}
+
+size_t sort_res_bytes() { return sizeof(SortRes); }
+
+}  // namespace sof
