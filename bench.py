@@ -126,14 +126,14 @@ def cpu_baseline(ds, pr, n_sample_proj: int):
     return ds.n * n_sample_proj / dt, dt
 
 
-def extra_legs(S, torch, dev, forest_trees=2, only=None):
+def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
     64 projections/node, T=1024), and one tree grown to purity (tree_small)."""
     from paper_2603_00326_b300 import datagen as G
     out = {}
     if only not in (None, "frontier"):
-        return _later_legs(S, torch, dev, forest_trees, only, out)
+        return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees)
     ds_np = G.frontier_1m()
     p = G.WORKLOAD_PARAMS["frontier_1m"]
     idx_np, off_np = G.frontier_nodes(ds_np.n, p["n_nodes"])
@@ -193,27 +193,28 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None):
     del dd, idx, off, ws, outb, views
     if only == "frontier":
         return out
-    return _later_legs(S, torch, dev, forest_trees, only, out)
+    return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees)
 
 
-def _later_legs(S, torch, dev, forest_trees, only, out):
+def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1):
     from paper_2603_00326_b300 import datagen as G
-    # one tree to purity
-    ts = G.tree_small()
-    tp = G.WORKLOAD_PARAMS["tree_small"]
-    dd = S.DeviceDataset(torch.from_numpy(ts.X).to(dev), torch.from_numpy(ts.y).to(dev), 2)
-    root = torch.from_numpy(G.all_indices(ts.n)).to(dev)
-    prm = S.tree_params(tp["n_proj"], tp["lam"], tp["cap"], 256, tp["sort_below"], seed=G.PROJ_SEED_BASE)
-    S.so_train_tree(dd, root, prm)
-    times = []
-    for _ in range(5):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        tr = S.so_train_tree(dd, root, prm)
-        times.append(time.perf_counter() - t0)
-    out["tree_small"] = {"train_s": min(times), "median_s": statistics.median(times), "nodes": tr.n_nodes,
-                         "depth": int(tr.depth.max())}
-    del dd, root
+    if only in (None, "tree"):
+        # one tree to purity
+        ts = G.tree_small()
+        tp = G.WORKLOAD_PARAMS["tree_small"]
+        dd = S.DeviceDataset(torch.from_numpy(ts.X).to(dev), torch.from_numpy(ts.y).to(dev), 2)
+        root = torch.from_numpy(G.all_indices(ts.n)).to(dev)
+        prm = S.tree_params(tp["n_proj"], tp["lam"], tp["cap"], 256, tp["sort_below"], seed=G.PROJ_SEED_BASE)
+        S.so_train_tree(dd, root, prm)
+        times = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tr = S.so_train_tree(dd, root, prm)
+            times.append(time.perf_counter() - t0)
+        out["tree_small"] = {"train_s": min(times), "median_s": statistics.median(times), "nodes": tr.n_nodes,
+                             "depth": int(tr.depth.max())}
+        del dd, root
     if forest_trees > 0 and only in (None, "forest"):
         from paper_2603_00326_b300 import forest as F
         fs = G.forest_2m()
@@ -229,7 +230,26 @@ def _later_legs(S, torch, dev, forest_trees, only, out):
                             "projected_forest_s": secs / forest_trees * fp["n_trees"],
                             "mean_nodes": float(np.mean([t.n_nodes for t in trees])),
                             "max_depth": int(max(int(t.depth.max()) for t in trees))}
-        del dd
+        del dd, trees
+    if wide_trees > 0 and only in (None, "wide"):
+        # wide count-like data: n=500k, d=4096, 90% zeros, 5 classes, grown to purity
+        ws_np = G.wide_counts()
+        wp = G.WORKLOAD_PARAMS["wide_counts"]
+        dd = S.DeviceDataset(torch.from_numpy(ws_np.X).to(dev), torch.from_numpy(ws_np.y).to(dev), 5)
+        root = torch.from_numpy(G.all_indices(ws_np.n)).to(dev)
+        prm = S.tree_params(wp["n_proj"], wp["lam"], wp["cap"], wp["n_bins"], wp["sort_below"],
+                            seed=G.PROJ_SEED_BASE + 4)
+        S.so_train_tree(dd, root, S.tree_params(8, 1.5, 8, 256, 1024, seed=1, max_depth=3))  # warm-up
+        times = []
+        for _ in range(wide_trees):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tr = S.so_train_tree(dd, root, prm)
+            times.append(time.perf_counter() - t0)
+        out["wide_counts"] = {"train_s": min(times), "trees": wide_trees, "nodes": tr.n_nodes,
+                              "depth": int(tr.depth.max())}
+        del dd, root
+    torch.cuda.empty_cache()
     return out
 
 
@@ -240,7 +260,8 @@ def run_leg(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     S.lib()
-    out = extra_legs(S, torch, dev, args.forest_trees if args.leg == "forest" else 0, only=args.leg)
+    out = extra_legs(S, torch, dev, args.forest_trees if args.leg == "forest" else 0, only=args.leg,
+                     wide_trees=args.wide_trees if args.leg == "wide" else 0)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
     return 0
 
@@ -403,7 +424,7 @@ def run_ours(args):
                   "n_left": int(rec["n_left"])},
     }
     if rank == 0 and world == 1 and not args.no_extras:
-        line["extras"] = extra_legs(S, torch, dev, args.forest_trees)
+        line["extras"] = extra_legs(S, torch, dev, args.forest_trees, wide_trees=args.wide_trees)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt = cpu_baseline(ds_np, pr, 32)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -426,10 +447,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the frontier, tree and forest legs")
-    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest"],
+    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest", "wide"],
                     help="run one secondary leg alone and print its JSON")
     ap.add_argument("--forest-trees", type=int, default=2,
                     help="trees of the n=2M, d=256 forest timed in the extras (0 skips)")
+    ap.add_argument("--wide-trees", type=int, default=1,
+                    help="timed trees of the n=500k, d=4096 wide count-like workload (0 skips)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -25,6 +25,7 @@ sizes the oracle finishes in seconds.
 from __future__ import annotations
 
 import dataclasses
+import os
 from typing import Optional
 
 import numpy as np
@@ -179,21 +180,33 @@ def forest_2m(n: int = 2 * 1024 * 1024, d: int = 256, seed: int = DATA_SEED_BASE
     return Dataset(X, y, 2, "forest_2m")
 
 
+def _wide_block(X: np.ndarray, f0: int, f1: int, ss: np.random.SeedSequence) -> None:
+    rng = np.random.default_rng(ss)
+    n = X.shape[1]
+    nz = rng.random((f1 - f0, n), dtype=np.float32) < np.float32(0.1)
+    k = int(nz.sum())
+    # zero-truncated Poisson(3) by rejection of zeros
+    vals = rng.poisson(3.0, size=k)
+    while True:
+        zero = vals == 0
+        if not zero.any():
+            break
+        vals[zero] = rng.poisson(3.0, size=int(zero.sum()))
+    sub = X[f0:f1]
+    sub[nz] = vals.astype(np.float32)
+
+
 def wide_counts(n: int = 500_000, d: int = 4096, seed: int = DATA_SEED_BASE + 4) -> Dataset:
-    rng = _rng(seed)
+    """Blocks of 64 features each draw from their own child stream of the
+    seed, so the blocks can be filled by a thread pool in any order."""
+    from concurrent.futures import ThreadPoolExecutor
     X = np.zeros((d, n), dtype=np.float32)
-    for f in range(d):
-        nz = rng.random(n) < 0.1
-        k = int(nz.sum())
-        # zero-truncated Poisson(3) by rejection of zeros
-        vals = rng.poisson(3.0, size=k)
-        while True:
-            zero = vals == 0
-            if not zero.any():
-                break
-            vals[zero] = rng.poisson(3.0, size=int(zero.sum()))
-        X[f, nz] = vals.astype(np.float32)
-    y = argmax_sparse_labels(rng, X, 5, 16, 0.5)
+    blk = 64
+    starts = list(range(0, d, blk))
+    children = np.random.SeedSequence(seed).spawn(len(starts) + 1)
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(lambda a: _wide_block(X, a[0], min(d, a[0] + blk), a[1]), zip(starts, children[:-1])))
+    y = argmax_sparse_labels(np.random.default_rng(children[-1]), X, 5, 16, 0.5)
     return Dataset(X, y, 5, "wide_counts")
 
 
