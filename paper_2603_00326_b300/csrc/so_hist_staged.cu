@@ -30,17 +30,65 @@
 
 namespace sof {
 
-constexpr int kStThreads = 512;          // threads of the staged kernels (16 warps)
+constexpr int kStThreads = 1024;         // threads of the staged kernels (32 warps, one CTA per SM)
 constexpr int kStWarps = kStThreads / 32;
-constexpr int kStEpt = 32;               // staged elements per thread per tile (registers), histograms
-constexpr int kMmEpt = 16;               // the same for min / max (smaller tile: two CTAs per SM)
-constexpr int kStUMax = kStThreads * kStEpt / 64;  // rows of a histogram tile at St = 64 -> 256
-constexpr int kMmUMax = kStThreads * kMmEpt / 64;  // rows of a min / max tile at St = 64 -> 128
+constexpr int kTileF = 8192;             // floats per tile buffer (32 KB); two buffers
+constexpr int kStUMax = kTileF / 64;     // rows of a tile at St = 64 -> 128
+constexpr int kMmUMax = kStUMax;
 constexpr int kStMaxWords = 2048;        // feature bitmap words (d <= 65536)
-constexpr int kMmPPW = 16;               // min/max: projections per warp
+constexpr int kMmPPW = 8;                // min/max: projections per warp
 constexpr int kMmGroup = kStWarps * kMmPPW;  // 256 projections per min/max group
+constexpr int kHistPGMax = 64;           // histogram projections per item (two per warp)
+constexpr int kHistPPW = kHistPGMax / kStWarps;  // histogram projections per warp
+constexpr int kMaxItem = 16384;          // samples per item (label bytes kept in shared memory)
 constexpr float kMagic = 12582912.0f;    // 1.5 * 2^23
 constexpr float kCondLimit = 262144.0f;  // 2^18
+
+// ---- asynchronous global -> shared copies (sm_80+ cp.async) ------------------
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ---- shared-memory accesses by 32-bit shared address --------------------------
+// The inner loops address shared memory with 32-bit offsets in the shared
+// window directly (no generic-pointer arithmetic).
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ float4 lds_f4(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds_f2(unsigned a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint4 lds_u4(unsigned a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ unsigned lds_u32(unsigned a) {
+  unsigned v;
+  asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ unsigned lds_u16(unsigned a) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];\n" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void reds_add(unsigned a, unsigned v) {
+  asm volatile("red.shared.add.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
+}
 
 // ---- packed FP32x2 (sm_100+ PTX) ------------------------------------------
 // Pairs are formed and split with mov.b64 so they stay register pairs.
@@ -173,11 +221,13 @@ __device__ __forceinline__ int row_of(int f, const uint32_t* s_bits, const int* 
   return s_wpre[f >> 5] + __popc(s_bits[f >> 5] & ((1u << (f & 31)) - 1u));
 }
 
-// Projection descriptors of the group in shared memory: k, row of each
-// non-zero (ascending feature order), sign as a float multiplier.
+// Projection descriptors of the group in shared memory: k, and per non-zero
+// (ascending feature order) a packed word with the tile byte offset
+// row * St * 4 in the low 16 bits (U * St <= 8192 floats) and the sign in
+// bit 31.
 template <int KMAX>
-__device__ __forceinline__ void build_desc(const ProjView& pv, int64_t qbase, int np, int d, const uint32_t* s_bits,
-                                           const int* s_wpre, int* s_dk, int16_t* s_drow, float* s_dsg) {
+__device__ __forceinline__ void build_desc(const ProjView& pv, int64_t qbase, int np, int d, int St,
+                                           const uint32_t* s_bits, const int* s_wpre, int* s_dk, uint32_t* s_dpk) {
   for (int e = threadIdx.x; e < np * KMAX; e += kStThreads) {
     const int p = e / KMAX, jj = e - (e / KMAX) * KMAX;
     const int rb = pv.beg[qbase + p];
@@ -187,82 +237,99 @@ __device__ __forceinline__ void build_desc(const ProjView& pv, int64_t qbase, in
     if (jj < k) {
       int f = pv.feat[rb + jj];
       f = (f < 0 || f >= d) ? 0 : f;
-      s_drow[p * KMAX + jj] = (int16_t)row_of(f, s_bits, s_wpre);
-      s_dsg[p * KMAX + jj] = pv.sign[rb + jj] == 1 ? 1.0f : -1.0f;
+      s_dpk[p * KMAX + jj] = (uint32_t)(row_of(f, s_bits, s_wpre) * St * 4) | (pv.sign[rb + jj] == 1 ? 0u : 0x80000000u);
     }
   }
 }
 
-// ---- tile staging through registers (prefetch of the next tile) -------------
-// Scalar form: thread owns tile column i = tid % St and rows tid/St + k*(NT/St),
-// one gather per element.  Vector form (a full tile of consecutive, 16-byte
-// aligned samples): thread owns float4 column tid % (St/4).  Threads tid < St
-// also fetch the label of tile position tid.
-template <int EPT>
-struct TileLoader {
-  float pre[EPT];
-  int ylab;  // label of position tid (tid < St), -1 for padding
-  __device__ __forceinline__ void load(const DatasetView& ds, const int32_t* __restrict__ idx, int64_t tbeg,
-                                       int64_t tend, int St, int U, const int* s_rowfeat, bool vec) {
-    if (vec) {
-      const int nq = St >> 2;
-      const int q = threadIdx.x & (nq - 1);
-      const int r0 = threadIdx.x / nq;
-      const int rstep = kStThreads / nq;
-      const int64_t sid0 = idx[tbeg];
-#pragma unroll
-      for (int k = 0; k < EPT / 4; ++k) {
-        const int r = r0 + k * rstep;
-        if (r < U) {
-          const float4 v = __ldg(reinterpret_cast<const float4*>(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid0) + q);
-          pre[4 * k] = v.x;
-          pre[4 * k + 1] = v.y;
-          pre[4 * k + 2] = v.z;
-          pre[4 * k + 3] = v.w;
-        }
-      }
-      if (threadIdx.x < St) ylab = ds.y[sid0 + threadIdx.x];
-    } else {
-      const int i = threadIdx.x % St;
-      const int r0 = threadIdx.x / St;
-      const int rstep = kStThreads / St;
-      const int64_t pos = tbeg + i;
-      const bool valid = pos < tend;
-      // padding positions repeat the tile's first sample (min / max unchanged)
-      const int64_t sid = safe_sample(idx[valid ? pos : tbeg], ds.n);
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int r = r0 + k * rstep;
-        if (r < U) pre[k] = __ldg(ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid);
-      }
-      if (threadIdx.x < St) ylab = valid ? (int)ds.y[sid] : -1;
+// ---- tile staging with asynchronous copies ------------------------------------
+// A tile is U rows (the item's features, ascending) by St samples, row-major
+// in shared memory.  Vector form (a full tile of consecutive samples, 16-byte
+// aligned): 16-byte copies along each row.  Gather form: thread owns column
+// i = tid % St and rows tid/St + k*(NT/St), one 4-byte copy per element;
+// columns past the item's end repeat its first sample (min / max unchanged;
+// their labels are marked invalid).  Nothing passes through registers.
+__device__ __forceinline__ void tile_issue(const DatasetView& ds, const int32_t* __restrict__ idx, int64_t tbeg,
+                                           int64_t tend, int St, int U, const int* s_rowfeat, bool vec,
+                                           float* dst) {
+  if (vec) {
+    const int lq = __ffs(St) - 3;  // log2(St / 4)
+    const int total = U << lq;
+    const int64_t sid0 = idx[tbeg];
+    for (int e = threadIdx.x; e < total; e += kStThreads) {
+      const int r = e >> lq, q = e & ((1 << lq) - 1);
+      cp_async16(dst + r * St + 4 * q, ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid0 + 4 * q);
     }
+  } else {
+    const int i = threadIdx.x & (St - 1);
+    const int rstep = kStThreads / St;
+    const int64_t pos = tbeg + i;
+    const int64_t sid = safe_sample(idx[pos < tend ? pos : tbeg], ds.n);
+    const float* xs = ds.X + sid;
+    for (int r = threadIdx.x / St; r < U; r += rstep) cp_async4(dst + r * St + i, xs + (int64_t)s_rowfeat[r] * ds.ld);
   }
-  __device__ __forceinline__ void store(float* s_tile, int St, int U, bool vec) const {
-    if (vec) {
-      const int nq = St >> 2;
-      const int q = threadIdx.x & (nq - 1);
-      const int r0 = threadIdx.x / nq;
-      const int rstep = kStThreads / nq;
-#pragma unroll
-      for (int k = 0; k < EPT / 4; ++k) {
-        const int r = r0 + k * rstep;
-        if (r < U)
-          reinterpret_cast<float4*>(s_tile + r * St)[q] =
-              make_float4(pre[4 * k], pre[4 * k + 1], pre[4 * k + 2], pre[4 * k + 3]);
-      }
-    } else {
-      const int i = threadIdx.x % St;
-      const int r0 = threadIdx.x / St;
-      const int rstep = kStThreads / St;
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int r = r0 + k * rstep;
-        if (r < U) s_tile[r * St + i] = pre[k];
-      }
-    }
-  }
+}
+
+
+// Per-thread copy plan of an item's tiles.  Every tile of an item has the same
+// rows and width and only its first sample moves, so the thread's source and
+// destination offsets are fixed once per item.  Vector form: the thread's (at
+// most two, U * St / 4 <= 2 * kStThreads) 16-byte chunks.  Gather form: the
+// thread's tile column and rows tid/St + k*(NT/St); the element offsets of the
+// rows (feature * ld) sit in shared memory.
+struct Stager {
+  const float* src0;
+  const float* src1;
+  int dst0, dst1;
+  int col;
+  bool vec;
 };
+
+__device__ __forceinline__ Stager stager_init(const DatasetView& ds, const int32_t* __restrict__ idx,
+                                              const ItemPos& it, int St, int U, const int* s_rowfeat, bool contig) {
+  Stager sg;
+  sg.vec = contig;
+  sg.col = threadIdx.x & (St - 1);
+  sg.src0 = sg.src1 = nullptr;
+  sg.dst0 = sg.dst1 = 0;
+  if (contig) {
+    const int lq = __ffs(St) - 3;  // log2(St / 4)
+    const int total = U << lq;
+    const int64_t sid0 = idx[it.beg];
+    const int e0 = threadIdx.x, e1 = threadIdx.x + kStThreads;
+    if (e0 < total) {
+      const int r = e0 >> lq, q = e0 & ((1 << lq) - 1);
+      sg.src0 = ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid0 + 4 * q;
+      sg.dst0 = r * St + 4 * q;
+    }
+    if (e1 < total) {
+      const int r = e1 >> lq, q = e1 & ((1 << lq) - 1);
+      sg.src1 = ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid0 + 4 * q;
+      sg.dst1 = r * St + 4 * q;
+    }
+  }
+  return sg;
+}
+
+// Issues the copies of tile t into buf.  A full tile of an aligned run of
+// consecutive samples takes the vector form; any other tile gathers, columns
+// past the item's end repeating its first sample.
+__device__ __forceinline__ void stager_issue(const Stager& sg, const DatasetView& ds, const int32_t* __restrict__ idx,
+                                             const ItemPos& it, int t, int St, int U, const int64_t* s_rowoff,
+                                             float* buf) {
+  const int64_t nb = it.beg + (int64_t)t * St;
+  if (sg.vec && it.end - nb >= St) {
+    const int64_t o = (int64_t)t * St;
+    if (sg.src0) cp_async16(buf + sg.dst0, sg.src0 + o);
+    if (sg.src1) cp_async16(buf + sg.dst1, sg.src1 + o);
+  } else {
+    const int64_t pos = nb + sg.col;
+    const int64_t sid = safe_sample(idx[pos < it.end ? pos : nb], ds.n);
+    const float* xs = ds.X + sid;
+    const int rstep = kStThreads / St;
+    for (int r = threadIdx.x / St; r < U; r += rstep) cp_async4(buf + r * St + sg.col, xs + s_rowoff[r]);
+  }
+}
 
 // Whether the item's samples are one run of consecutive indices that the
 // vector form may read directly (all threads call; one barrier).
@@ -275,11 +342,10 @@ __device__ __forceinline__ bool item_contiguous(const DatasetView& ds, const int
   return __syncthreads_and(ok) != 0;
 }
 
-template <int EPT>
 __device__ __forceinline__ int choose_st(int U) {
-  // U * St <= kStThreads * EPT, St in {64, 128, 256}
-  if (U * 256 <= kStThreads * EPT) return 256;
-  if (U * 128 <= kStThreads * EPT) return 128;
+  // U * St <= kTileF, St in {64, 128, 256}
+  if (U * 256 <= kTileF) return 256;
+  if (U * 128 <= kTileF) return 128;
   return 64;
 }
 
@@ -370,15 +436,14 @@ struct ItemScanF {
   const int64_t* off;
   const int32_t* ng1;
   const int32_t* ng2;
-  int64_t S;
+  int64_t S1, S2;  // samples per item of the min / max and the histogram kernels
   int64_t* item_off1;
   int64_t* item_off2;
   __device__ V4 value(int64_t h) const {
     if (h >= plan_total->x) return V4{0, 0, 0, 0};
     const int j = hist_nodes[h];
     const int64_t nv = off[j + 1] - off[j];
-    const int64_t ch = (nv + S - 1) / S;
-    return V4{ch * ng1[h], ch * ng2[h], 0, 0};
+    return V4{(nv + S1 - 1) / S1 * ng1[h], (nv + S2 - 1) / S2 * ng2[h], 0, 0};
   }
   __device__ void apply(int64_t h, V4 ex) const {
     if (h >= plan_total->x) return;
@@ -387,90 +452,182 @@ struct ItemScanF {
   }
 };
 
-// ---- k_mm_staged: min / max -------------------------------------------------
-// Per (projection, tile): the warp of the projection evaluates every sample
-// pair of the tile with the projection's rows and signs in registers (the
-// loop is specialised on the projection's non-zero count K); per-lane running
-// minima and maxima live in shared memory until the item ends.
-template <int K, int NPS>
-__device__ __forceinline__ void mm_tile(const float* __restrict__ s_tile, const int16_t* drow, const float* dsg,
-                                        int St, int lane, float& mn, float& mx) {
-  int roff[K];
-  float2 sg[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    roff[j] = drow[j] * St + 2 * lane;
-    sg[j] = make_float2(dsg[j], dsg[j]);
+// Static assignment of an item's projections to warps, balanced by non-zero
+// count: projections ranked by k (descending, counting sort) are dealt to the
+// warps in snake order (0..31, 31..0, ...).  s_assign[w * nslot + s] is the
+// s-th projection of warp w, or -1.  Needs s_dk complete; the caller syncs
+// before reading s_assign.
+__device__ __forceinline__ int assign_snake(int np, const int* s_dk, int* s_kcnt, int* s_assign) {
+  const int nslot = (np + kStWarps - 1) / kStWarps;
+  for (int e = threadIdx.x; e < kMaxCap + 1; e += kStThreads) s_kcnt[e] = 0;
+  for (int e = threadIdx.x; e < nslot * kStWarps; e += kStThreads) s_assign[e] = -1;
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += kStThreads) atomicAdd(&s_kcnt[s_dk[p]], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = kMaxCap; k >= 0; --k) {
+      const int c = s_kcnt[k];
+      s_kcnt[k] = run;
+      run += c;
+    }
   }
-  // NPS > 0: the St/64 pair-steps are unrolled (St = 64 * NPS); NPS = 0: rolled
-  const int nps = NPS > 0 ? NPS : (St >> 6);
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += kStThreads) {
+    const int r = atomicAdd(&s_kcnt[s_dk[p]], 1);
+    const int round = r / kStWarps, j = r - round * kStWarps;
+    const int w = (round & 1) ? (kStWarps - 1 - j) : j;
+    s_assign[w * nslot + round] = p;
+  }
+  return nslot;
+}
+
+// ---- k_mm_staged: min / max -------------------------------------------------
+// Projection descriptors are packed words: the tile offset (row * St) of a
+// non-zero in the low 16 bits and its sign in bit 31.  The loop over a
+// projection's non-zeros is not specialised: each term is one broadcast
+// descriptor load, then NPS packed FP32x2 fused multiply-adds (one per sample
+// pair-step of the tile), so a warp's work per tile needs no dispatch.
+// fma(+-1, x, acc) rounds exactly like acc + (+-x).
+__device__ __forceinline__ float desc_sign(uint32_t w) { return __uint_as_float((w & 0x80000000u) | 0x3f800000u); }
+
+// Lane layout of a tile of St samples: NQ steps of 32*V consecutive samples,
+// V consecutive samples per lane in each step (vector loads of V floats):
+// sample(q, v) = 32*V*q + V*lane + v.  St = 64 -> (V, NQ) = (2, 1),
+// St = 128 -> (4, 1), St = 256 -> (4, 2).
+template <int V, int NQ>
+__device__ __forceinline__ void project_term(unsigned base, uint32_t w, float (&acc)[V * NQ]) {
+  const float s = desc_sign(w);
+  const unsigned row = base + (w & 0xffffu);
 #pragma unroll
-  for (int q = 0; q < (NPS > 0 ? NPS : 1); ++q) {
-    for (int r = 0; r < (NPS > 0 ? 1 : nps); ++r) {
-      const int ps = 64 * (NPS > 0 ? q : r);
-      float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
-      mn = fminf(mn, fminf(acc.x, acc.y));
-      mx = fmaxf(mx, fmaxf(acc.x, acc.y));
+  for (int q = 0; q < NQ; ++q) {
+    if (V == 4) {
+      const float4 x = lds_f4(row + 512 * q);
+      acc[4 * q] = __fmaf_rn(s, x.x, acc[4 * q]);
+      acc[4 * q + 1] = __fmaf_rn(s, x.y, acc[4 * q + 1]);
+      acc[4 * q + 2] = __fmaf_rn(s, x.z, acc[4 * q + 2]);
+      acc[4 * q + 3] = __fmaf_rn(s, x.w, acc[4 * q + 3]);
+    } else {
+      const float2 x = lds_f2(row + 256 * q);
+      acc[2 * q] = __fmaf_rn(s, x.x, acc[2 * q]);
+      acc[2 * q + 1] = __fmaf_rn(s, x.y, acc[2 * q + 1]);
     }
   }
 }
 
-// Dispatch on (non-zero count, pair-steps per tile); counts above 16 use the
-// rolled form.
-template <int KMAX>
-__device__ __forceinline__ void mm_tile_k(int k, const float* s_tile, const int16_t* drow, const float* dsg, int St,
-                                          int lane, float& mn, float& mx) {
-  const int nps = St >> 6;
-  const int key = k * 8 + (nps == 4 ? 2 : nps == 2 ? 1 : 0);
-  switch (key) {
-#define SOF_MM_CASE(N)                                                                                        \
-  case N * 8 + 0:                                                                                             \
-    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 1>(s_tile, drow, dsg, St, lane, mn, mx);                      \
-    return;                                                                                                   \
-  case N * 8 + 1:                                                                                             \
-    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 2>(s_tile, drow, dsg, St, lane, mn, mx);                      \
-    return;                                                                                                   \
-  case N * 8 + 2:                                                                                             \
-    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 4>(s_tile, drow, dsg, St, lane, mn, mx);                      \
-    return;
-    SOF_MM_CASE(1) SOF_MM_CASE(2) SOF_MM_CASE(3) SOF_MM_CASE(4) SOF_MM_CASE(5) SOF_MM_CASE(6) SOF_MM_CASE(7)
-    SOF_MM_CASE(8) SOF_MM_CASE(9) SOF_MM_CASE(10) SOF_MM_CASE(11) SOF_MM_CASE(12) SOF_MM_CASE(13)
-    SOF_MM_CASE(14) SOF_MM_CASE(15) SOF_MM_CASE(16)
-#undef SOF_MM_CASE
-    default:
-      break;
+// The projection's terms in order: descriptor words four at a time (16-byte
+// loads; rows are padded to a multiple of 8 words), a warp-uniform exit after
+// each term.  tile and dpk are shared addresses of the tile buffer and of the
+// projection's descriptor row.
+template <int V, int NQ>
+__device__ __forceinline__ void project_tile(unsigned tile, unsigned dpk, int k, int lane, float (&acc)[V * NQ]) {
+  const unsigned base = tile + 4u * V * lane;
+#pragma unroll
+  for (int i = 0; i < V * NQ; ++i) acc[i] = 0.0f;
+  for (int j0 = 0; j0 < k; j0 += 4) {
+    const uint4 w = lds_u4(dpk + 4u * j0);
+    project_term<V, NQ>(base, w.x, acc);
+    if (j0 + 1 >= k) break;
+    project_term<V, NQ>(base, w.y, acc);
+    if (j0 + 2 >= k) break;
+    project_term<V, NQ>(base, w.z, acc);
+    if (j0 + 3 >= k) break;
+    project_term<V, NQ>(base, w.w, acc);
   }
-  switch (k) {
-#define SOF_MM_ROLLED(N) \
-  case N:                \
-    if (N <= KMAX) mm_tile<(N <= KMAX ? N : 1), 0>(s_tile, drow, dsg, St, lane, mn, mx); \
-    break;
-    SOF_MM_ROLLED(17) SOF_MM_ROLLED(18) SOF_MM_ROLLED(19) SOF_MM_ROLLED(20) SOF_MM_ROLLED(21) SOF_MM_ROLLED(22)
-    SOF_MM_ROLLED(23) SOF_MM_ROLLED(24) SOF_MM_ROLLED(25) SOF_MM_ROLLED(26) SOF_MM_ROLLED(27) SOF_MM_ROLLED(28)
-    SOF_MM_ROLLED(29) SOF_MM_ROLLED(30) SOF_MM_ROLLED(31) SOF_MM_ROLLED(32)
-#undef SOF_MM_ROLLED
-    default:
-      break;
+}
+
+// Label byte offsets (class * 4) of the lane's samples, in project_tile's
+// order, from the item's label bytes (0xFF marks padding and labels outside
+// [0, C); those get a very negative offset that the address clamp sends to
+// the trash word).
+__device__ __forceinline__ int label_off8(unsigned b) { return b != 0xFFu ? (int)(b * 4u) : (INT_MIN / 2); }
+
+template <int V, int NQ>
+__device__ __forceinline__ void tile_labels(unsigned lab, int lane, int (&yo)[V * NQ]) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (V == 4) {
+      const unsigned w = lds_u32(lab + 128 * q + 4 * lane);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yo[4 * q + v] = label_off8((w >> (8 * v)) & 0xffu);
+    } else {
+      const unsigned w = lds_u16(lab + 64 * q + 2 * lane);
+      yo[2 * q] = label_off8(w & 0xffu);
+      yo[2 * q + 1] = label_off8(w >> 8);
+    }
+  }
+}
+
+// The item's tile loop, one instantiation per tile width St = 32 * V * NQ
+// (the same for every warp of the CTA).  Three tile buffers: tile tt+2 is
+// copied while tile tt is evaluated, one barrier per tile.  Warp w evaluates
+// its assigned projections; per-lane running minima and maxima of each
+// projection live in shared memory (only this warp touches them).
+template <int V, int NQ>
+__device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
+                                        int U, bool contig, float* s_tile, const int* s_rowfeat,
+                                        const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk,
+                                        const uint32_t* s_dpk, int kmax, float* s_pmin, float* s_pmax, int lane,
+                                        int warp) {
+  constexpr int St = 32 * V * NQ;
+  const int ntile = (int)((it.end - it.beg + St - 1) / St);
+  const int* my = s_assign + warp * nslot;
+  for (int sl = 0; sl < nslot; ++sl) {
+    const int pl = my[sl];
+    if (pl < 0) break;
+    s_pmin[pl * 32 + lane] = INFINITY;
+    s_pmax[pl * 32 + lane] = -INFINITY;
+  }
+  const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig);
+  if (ntile > 0) stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
+  cp_async_commit();
+  if (ntile > 1) stager_issue(sg, ds, idx, it, 1, St, U, s_rowoff, s_tile + kTileF);
+  cp_async_commit();
+  int bc = 0, bi = 2;  // buffer of tile tt, buffer of tile tt + 2
+  for (int tt = 0; tt < ntile; ++tt) {
+    cp_async_wait1();
+    __syncthreads();  // tile tt visible; every warp done with tile tt-1
+    if (tt + 2 < ntile) stager_issue(sg, ds, idx, it, tt + 2, St, U, s_rowoff, s_tile + bi * kTileF);
+    cp_async_commit();
+    const unsigned tile = su32(s_tile) + 4u * kTileF * bc;
+    bc = bc == 2 ? 0 : bc + 1;
+    bi = bi == 2 ? 0 : bi + 1;
+    for (int sl = 0; sl < nslot; ++sl) {
+      const int pl = my[sl];
+      if (pl < 0) break;
+      float acc[V * NQ];
+      project_tile<V, NQ>(tile, su32(s_dpk) + 4u * pl * kmax, s_dk[pl], lane, acc);
+      float mn = s_pmin[pl * 32 + lane], mx = s_pmax[pl * 32 + lane];
+#pragma unroll
+      for (int i = 0; i < V * NQ; ++i) {
+        mn = fminf(mn, acc[i]);
+        mx = fmaxf(mx, acc[i]);
+      }
+      s_pmin[pl * 32 + lane] = mn;
+      s_pmax[pl * 32 + lane] = mx;
+    }
   }
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kStThreads, (KMAX <= 8 ? 2 : 1)) k_mm_staged(DatasetView ds, const int32_t* __restrict__ idx,
+__global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, const int32_t* __restrict__ idx,
                                                             ProjView pv, StagedPlan sp, uint32_t* mm) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
-  float* s_tile = reinterpret_cast<float*>(s_raw);                       // [kStThreads*kMmEpt]
-  float* s_pmin = s_tile + kStThreads * kMmEpt;                          // [kMmGroup*32]
-  float* s_pmax = s_pmin + kMmGroup * 32;                                // [kMmGroup*32]
-  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_pmax + kMmGroup * 32);  // [nw]
-  int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                     // [nw]
-  int* s_rowfeat = s_wpre + nw;                                          // [kStUMax]
-  int* s_dk = s_rowfeat + kStUMax;                                       // [kMmGroup]
-  float* s_dsg = reinterpret_cast<float*>(s_dk + kMmGroup);              // [kMmGroup*KMAX]
-  int16_t* s_drow = reinterpret_cast<int16_t*>(s_dsg + kMmGroup * KMAX); // [kMmGroup*KMAX]
+  float* s_tile = reinterpret_cast<float*>(s_raw);                         // [3][kTileF]
+  float* s_pmin = s_tile + 3 * kTileF;                                     // [kMmGroup*32]
+  float* s_pmax = s_pmin + kMmGroup * 32;                                  // [kMmGroup*32]
+  uint32_t* s_dpk = reinterpret_cast<uint32_t*>(s_pmax + kMmGroup * 32);   // [kMmGroup*KMAX]
+  int* s_dk = reinterpret_cast<int*>(s_dpk + kMmGroup * KMAX);             // [kMmGroup]
+  int* s_assign = s_dk + kMmGroup;                                         // [kMmGroup]
+  int* s_rowfeat = s_assign + kMmGroup;                                    // [kStUMax]
+  int64_t* s_rowoff = reinterpret_cast<int64_t*>(s_rowfeat + kStUMax);     // [kStUMax]
+  // the feature bitmap is only used while an item is set up, before tile 2
+  // is copied: it shares the third tile buffer
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_tile + 2 * kTileF);     // [nw]
+  int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                       // [nw]
   __shared__ int s_misc[kStWarps + 1];
+  __shared__ int s_kcnt[kMaxCap + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = pv.P;
   const int64_t n_items = items_total(sp);
@@ -479,35 +636,22 @@ __global__ void __launch_bounds__(kStThreads, (KMAX <= 8 ? 2 : 1)) k_mm_staged(D
     const int64_t qbase = (int64_t)it.j * P + it.p0;
     __syncthreads();  // previous item done with shared memory
     const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
-    build_desc<KMAX>(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_dk, s_drow, s_dsg);
-    for (int e = threadIdx.x; e < it.np * 32; e += kStThreads) {
-      s_pmin[e] = INFINITY;
-      s_pmax[e] = -INFINITY;
-    }
+    const int St = choose_st(U);
+    build_desc<KMAX>(pv, qbase, it.np, ds.d, St, s_bits, s_wpre, s_dk, s_dpk);
+    __syncthreads();  // s_dk and s_rowfeat complete
+    for (int r = threadIdx.x; r < U && r < kStUMax; r += kStThreads) s_rowoff[r] = (int64_t)s_rowfeat[r] * ds.ld;
+    const int nslot = assign_snake(it.np, s_dk, s_kcnt, s_assign);
     const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
     if (U <= kMmUMax) {
-      const int St = choose_st<kMmEpt>(U);
-      const int64_t len = it.end - it.beg;
-      const int64_t ntile = (len + St - 1) / St;
-      TileLoader<kMmEpt> ld;
-      bool vec = contig && len >= St;
-      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat, vec);
-      for (int64_t tt = 0; tt < ntile; ++tt) {
-        __syncthreads();
-        ld.store(s_tile, St, U, vec);
-        __syncthreads();
-        if (tt + 1 < ntile) {
-          const int64_t nb = it.beg + (tt + 1) * St;
-          vec = contig && (it.end - nb) >= St;
-          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat, vec);
-        }
-        for (int pl = warp; pl < it.np; pl += kStWarps) {
-          float mn = s_pmin[pl * 32 + lane], mx = s_pmax[pl * 32 + lane];
-          mm_tile_k<KMAX>(s_dk[pl], s_tile, s_drow + pl * KMAX, s_dsg + pl * KMAX, St, lane, mn, mx);
-          s_pmin[pl * 32 + lane] = mn;
-          s_pmax[pl * 32 + lane] = mx;
-        }
-      }
+      if (St == 256)
+        mm_item<4, 2>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
+                   lane, warp);
+      else if (St == 128)
+        mm_item<4, 1>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
+                   lane, warp);
+      else
+        mm_item<2, 1>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
+                   lane, warp);
     } else {
       // direct path for wide groups: each warp gathers its projections' features
       for (int pl = warp; pl < it.np; pl += kStWarps) {
@@ -544,105 +688,108 @@ __global__ void __launch_bounds__(kStThreads, (KMAX <= 8 ? 2 : 1)) k_mm_staged(D
 }
 
 // ---- k_hist_staged: class-count histograms -----------------------------------
-// Histogram layout in shared memory: [pl][B+1][C] int32, one spare bin per
-// projection, then a trash word.  Addresses are byte offsets clamped (as
-// unsigned) to the trash word, which absorbs padding positions (label offset
-// very negative), labels outside [0, C) and non-finite projected values.
+// 16-bit counters in shared memory, two projections per 32-bit word: the pair
+// (2i, 2i+1) shares a [B+1][C] array of words (one spare bin), projection 2i
+// in the low half, 2i+1 in the high half; then a trash word.  A warp's atomic
+// add touches one half only, so lanes of one instruction collide only on the
+// same (bin, class).  An item holds at most 65535 samples, so no counter
+// overflows.  Addresses are byte offsets clamped (as unsigned) to the trash
+// word, which absorbs padding positions (label offset very negative), labels
+// outside [0, C) and non-finite projected values.
 struct BinParams {
   float mn, W, inv_w, c;
-  unsigned hb;  // byte base of the projection's histogram minus magic*C*4 (mod 2^32)
+  unsigned hb;   // byte base of the projection pair's words minus magic*C*4 (mod 2^32)
+  unsigned inc;  // 1 or 1 << 16
   int fast;
 };
 
-template <int K, int NPS>
-__device__ __forceinline__ void hist_tile(const float* __restrict__ s_tile, const int* __restrict__ s_y4,
-                                          const int16_t* drow, const float* dsg, int St, int lane, const BinParams& bp,
-                                          unsigned C4, unsigned limit, char* s_histb) {
-  int roff[K];
-  float2 sg[K];
+template <int V, int NQ>
+__device__ __forceinline__ void hist_tile_fast(unsigned tile, unsigned lab, unsigned dpk, int k, int lane,
+                                               const BinParams& bp, unsigned C4, unsigned limit) {
+  float acc[V * NQ];
+  int yo[V * NQ];
+  project_tile<V, NQ>(tile, dpk, k, lane, acc);
+  tile_labels<V, NQ>(lab, lane, yo);
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    roff[j] = drow[j] * St + 2 * lane;
-    sg[j] = make_float2(dsg[j], dsg[j]);
-  }
-  const float2 inv2 = make_float2(bp.inv_w, bp.inv_w);
-  const float2 c2 = make_float2(bp.c, bp.c);
-  const float2 m2 = make_float2(kMagic, kMagic);
-  const float2 m1 = make_float2(1.0f - kMagic, 1.0f - kMagic);
-  const int nps = NPS > 0 ? NPS : (St >> 6);
-#pragma unroll
-  for (int q = 0; q < (NPS > 0 ? NPS : 1); ++q) {
-    for (int r = 0; r < (NPS > 0 ? 1 : nps); ++r) {
-      const int ps = 64 * (NPS > 0 ? q : r);
-      float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int j = 0; j < K; ++j) acc = ffma2(sg[j], *reinterpret_cast<const float2*>(s_tile + roff[j] + ps), acc);
-      const int2 y4 = *reinterpret_cast<const int2*>(s_y4 + ps + 2 * lane);
-      const float2 e = ffma2(acc, inv2, c2);
-      const float2 tq = fadd2(e, m2);
-      const float2 q1 = fadd2(tq, m1);
-      // t_{q+1} = min + (q+1)*W with two roundings (scalar: not fused)
-      const float tbx = __fadd_rn(bp.mn, __fmul_rn(q1.x, bp.W));
-      const float tby = __fadd_rn(bp.mn, __fmul_rn(q1.y, bp.W));
-      unsigned ax = __float_as_uint(tq.x) * C4 + (bp.hb + (unsigned)y4.x);
-      unsigned ay = __float_as_uint(tq.y) * C4 + (bp.hb + (unsigned)y4.y);
-      if (tbx <= acc.x) ax += C4;
-      if (tby <= acc.y) ay += C4;
-      ax = min(ax, limit);
-      ay = min(ay, limit);
-      atomicAdd(reinterpret_cast<int*>(s_histb + ax), 1);
-      atomicAdd(reinterpret_cast<int*>(s_histb + ay), 1);
-    }
-  }
-}
-
-template <int KMAX>
-__device__ __forceinline__ void hist_tile_k(int k, const float* s_tile, const int* s_y4, const int16_t* drow,
-                                            const float* dsg, int St, int lane, const BinParams& bp, unsigned C4,
-                                            unsigned limit, char* s_histb) {
-  const int nps = St >> 6;
-  const int key = k * 8 + (nps == 4 ? 2 : nps == 2 ? 1 : 0);
-  switch (key) {
-#define SOF_H_CASE(N)                                                                                               \
-  case N * 8 + 0:                                                                                                   \
-    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 1>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb);    \
-    return;                                                                                                         \
-  case N * 8 + 1:                                                                                                   \
-    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 2>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb);    \
-    return;                                                                                                         \
-  case N * 8 + 2:                                                                                                   \
-    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 4>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb);    \
-    return;
-    SOF_H_CASE(1) SOF_H_CASE(2) SOF_H_CASE(3) SOF_H_CASE(4) SOF_H_CASE(5) SOF_H_CASE(6) SOF_H_CASE(7)
-    SOF_H_CASE(8) SOF_H_CASE(9) SOF_H_CASE(10) SOF_H_CASE(11) SOF_H_CASE(12) SOF_H_CASE(13) SOF_H_CASE(14)
-    SOF_H_CASE(15) SOF_H_CASE(16)
-#undef SOF_H_CASE
-    default:
-      break;
-  }
-  switch (k) {
-#define SOF_H_ROLLED(N) \
-  case N:               \
-    if (N <= KMAX) hist_tile<(N <= KMAX ? N : 1), 0>(s_tile, s_y4, drow, dsg, St, lane, bp, C4, limit, s_histb); \
-    break;
-    SOF_H_ROLLED(17) SOF_H_ROLLED(18) SOF_H_ROLLED(19) SOF_H_ROLLED(20) SOF_H_ROLLED(21) SOF_H_ROLLED(22)
-    SOF_H_ROLLED(23) SOF_H_ROLLED(24) SOF_H_ROLLED(25) SOF_H_ROLLED(26) SOF_H_ROLLED(27) SOF_H_ROLLED(28)
-    SOF_H_ROLLED(29) SOF_H_ROLLED(30) SOF_H_ROLLED(31) SOF_H_ROLLED(32)
-#undef SOF_H_ROLLED
-    default:
-      break;
+  for (int i = 0; i < V * NQ; ++i) {
+    // q = round(v / W + c') by the 1.5 * 2^23 shift; then the exact boundary
+    // t_{q+1} = min + (q+1) * W with two roundings decides between q and q+1
+    const float tq = __fadd_rn(__fmaf_rn(acc[i], bp.inv_w, bp.c), kMagic);
+    const float q1 = __fadd_rn(tq, 1.0f - kMagic);
+    const float tb = __fadd_rn(bp.mn, __fmul_rn(q1, bp.W));
+    unsigned a = __float_as_uint(tq) * C4 + (bp.hb + (unsigned)yo[i]);
+    if (tb <= acc[i]) a += C4;
+    reds_add(min(a, limit), bp.inc);
   }
 }
 
 // exact estimate-and-correct rule for projections outside the fast condition
-__device__ __forceinline__ void hist_tile_slow(int k, const float* __restrict__ s_tile, const int* __restrict__ s_y4,
-                                               const int16_t* drow, const float* dsg, int St, int lane,
-                                               const BinParams& bp, int B, int C, int hbase, int32_t* s_hist) {
-  for (int i = lane; i < St; i += 32) {
-    float acc = 0.0f;
-    for (int j = 0; j < k; ++j) acc = __fmaf_rn(dsg[j], s_tile[drow[j] * St + i], acc);
-    const int y4 = s_y4[i];
-    if (y4 >= 0) atomicAdd(&s_hist[hbase + bin_of(acc, bp.mn, bp.W, bp.inv_w, B) * C + (y4 >> 2)], 1);
+template <int V, int NQ>
+__device__ __forceinline__ void hist_tile_slow(unsigned tile, unsigned lab, unsigned dpk, int k, int lane,
+                                               const BinParams& bp, int B, int C, int wbase, uint32_t* s_hist) {
+  float acc[V * NQ];
+  int yo[V * NQ];
+  project_tile<V, NQ>(tile, dpk, k, lane, acc);
+  tile_labels<V, NQ>(lab, lane, yo);
+#pragma unroll
+  for (int i = 0; i < V * NQ; ++i)
+    if (yo[i] >= 0) atomicAdd(&s_hist[wbase + bin_of(acc[i], bp.mn, bp.W, bp.inv_w, B) * C + (yo[i] >> 2)], bp.inc);
+}
+
+// The item's tile loop for tile width St = 32 * V * NQ.  Three tile buffers,
+// one barrier per tile; labels go through a register one tile ahead.  Warp w
+// evaluates its assigned projections (at most kHistPPW) with their bin
+// parameters in registers.
+template <int V, int NQ>
+__device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
+                                          int U, bool contig, float* s_tile, const uint8_t* s_lab, const int* s_rowfeat,
+                                          const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk, const uint32_t* s_dpk,
+                                          int kmax, const float4* s_bpf, const int4* s_bpi, int B, int HS,
+                                          unsigned C4, unsigned limit, uint32_t* s_hist, int lane, int warp) {
+  constexpr int St = 32 * V * NQ;
+  const int C = ds.C;
+  const int ntile = (int)((it.end - it.beg + St - 1) / St);
+  int pls[kHistPPW], ks[kHistPPW];
+  BinParams bps[kHistPPW];
+#pragma unroll
+  for (int sl = 0; sl < kHistPPW; ++sl) {
+    pls[sl] = sl < nslot ? s_assign[warp * nslot + sl] : -1;
+    const int pl = pls[sl] >= 0 ? pls[sl] : 0;
+    ks[sl] = pls[sl] >= 0 ? s_dk[pl] : 0;
+    const float4 bf = s_bpf[pl];
+    const int4 bi = s_bpi[pl];
+    // absolute shared address base: the unsigned wrap of the clamp is kept
+    // (a valid address stays below the shared window's end, a rejected one
+    // stays far above it)
+    bps[sl] = BinParams{bf.x, bf.y, bf.z, bf.w, su32(s_hist) + (unsigned)bi.x, (unsigned)bi.y, bi.z};
+  }
+  const unsigned limit_abs = su32(s_hist) + limit;
+  const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig);
+  if (ntile > 0) stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
+  cp_async_commit();
+  if (ntile > 1) stager_issue(sg, ds, idx, it, 1, St, U, s_rowoff, s_tile + kTileF);
+  cp_async_commit();
+  int bc = 0, bn = 1, bi = 2;  // buffers of tiles tt, tt + 1, tt + 2
+  for (int tt = 0; tt < ntile; ++tt) {
+    cp_async_wait1();
+    __syncthreads();  // tile tt visible; every warp done with tile tt-1
+    if (tt + 2 < ntile) stager_issue(sg, ds, idx, it, tt + 2, St, U, s_rowoff, s_tile + bi * kTileF);
+    cp_async_commit();
+    const unsigned tile = su32(s_tile) + 4u * kTileF * bc;
+    const unsigned lab = su32(s_lab) + (unsigned)(tt * St);
+    bc = bn;
+    bn = bi;
+    bi = bi == 2 ? 0 : bi + 1;
+#pragma unroll
+    for (int sl = 0; sl < kHistPPW; ++sl) {
+      if (pls[sl] >= 0) {
+        if (bps[sl].fast)
+          hist_tile_fast<V, NQ>(tile, lab, su32(s_dpk) + 4u * pls[sl] * kmax, ks[sl], lane, bps[sl], C4, limit_abs);
+        else
+          hist_tile_slow<V, NQ>(tile, lab, su32(s_dpk) + 4u * pls[sl] * kmax, ks[sl], lane, bps[sl], B, C, (pls[sl] >> 1) * HS,
+                              s_hist);
+      }
+    }
   }
 }
 
@@ -653,26 +800,31 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
   const int C = ds.C;
-  const int HS = (B + 1) * C;  // words per projection histogram
-  const int hist_words = ((PG * HS + 1) + 3) & ~3;
-  // every region starts on a 16-byte boundary (s_y4 is read as int2)
-  float* s_tile = reinterpret_cast<float*>(s_raw);                        // [kStThreads*kStEpt]
-  int* s_y4 = reinterpret_cast<int*>(s_tile + kStThreads * kStEpt);       // [256] label byte offset
-  int32_t* s_hist = s_y4 + 256;                                           // [PG*HS + 1 (trash)]
-  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_hist + hist_words);    // [nw]
-  int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                      // [nw]
-  int* s_rowfeat = s_wpre + nw;                                           // [kStUMax]
-  int* s_dk = s_rowfeat + kStUMax;                                        // [32]
-  float* s_dsg = reinterpret_cast<float*>(s_dk + 32);                     // [32*KMAX]
-  int16_t* s_drow = reinterpret_cast<int16_t*>(s_dsg + 32 * KMAX);        // [32*KMAX]
+  const int HS = (B + 1) * C;  // words per projection pair
+  const int npair = (PG + 1) >> 1;
+  const int hist_words = (npair * HS + 1 + 3) & ~3;
+  // every region starts on a 16-byte boundary
+  float* s_tile = reinterpret_cast<float*>(s_raw);                           // [3][kTileF]
+  uint8_t* s_lab = reinterpret_cast<uint8_t*>(s_tile + 3 * kTileF);          // [kMaxItem + 256] item labels
+  uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_lab + kMaxItem + 256);    // [hist_words]
+  uint32_t* s_dpk = s_hist + hist_words;                                     // [kHistPGMax*KMAX]
+  int* s_dk = reinterpret_cast<int*>(s_dpk + kHistPGMax * KMAX);             // [kHistPGMax]
+  int* s_assign = s_dk + kHistPGMax;                                         // [kHistPGMax]
+  int* s_rowfeat = s_assign + kHistPGMax;                                    // [kStUMax]
+  int64_t* s_rowoff = reinterpret_cast<int64_t*>(s_rowfeat + kStUMax);       // [kStUMax]
+  // the feature bitmap is only used while an item is set up, before tile 2
+  // is copied: it shares the third tile buffer
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_tile + 2 * kTileF);       // [nw]
+  int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                         // [nw]
+  __shared__ float4 s_bpf[kHistPGMax];  // min, W, 1/W, c
+  __shared__ int4 s_bpi[kHistPGMax];    // hb, inc, fast
   __shared__ int s_misc[kStWarps + 1];
-  __shared__ BinParams s_bp[32];
+  __shared__ int s_kcnt[kMaxCap + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = pv.P;
   const unsigned C4 = (unsigned)C * 4u;
-  const unsigned limit = (unsigned)(PG * HS) * 4u;  // byte offset of the trash word
+  const unsigned limit = (unsigned)(npair * HS) * 4u;  // byte offset of the trash word
   const unsigned magic_bits = __float_as_uint(kMagic);
-  char* s_histb = reinterpret_cast<char*>(s_hist);
   const int64_t n_items = items_total(sp);
   for (int64_t t = blockIdx.x; t < n_items; t += gridDim.x) {
     const ItemPos it = decode_item(sp, t, P);
@@ -683,53 +835,46 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
       for (int e = threadIdx.x; e < hist_words / 4; e += kStThreads) h4[e] = make_int4(0, 0, 0, 0);
     }
     const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
-    build_desc<KMAX>(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_dk, s_drow, s_dsg);
+    const int St = choose_st(U);
+    build_desc<KMAX>(pv, qbase, it.np, ds.d, St, s_bits, s_wpre, s_dk, s_dpk);
     if (threadIdx.x < it.np) {
       const int pl = threadIdx.x;
       const float mn = key2f(mm[(it.h * P + it.p0 + pl) * 2]);
       const float mx = key2f(mm[(it.h * P + it.p0 + pl) * 2 + 1]);
-      BinParams bp;
-      bp.mn = mn;
-      bp.W = bin_width(mn, mx, B);
-      bp.inv_w = __frcp_rn(bp.W);
-      bp.c = __fsub_rn(__fmul_rn(-mn, bp.inv_w), 0.75f);
+      const float W = bin_width(mn, mx, B);
+      const float inv_w = __frcp_rn(W);
+      const float c = __fsub_rn(__fmul_rn(-mn, inv_w), 0.75f);
       const float M = fmaxf(fabsf(mn), fabsf(mx));
-      bp.fast = (bp.W > 0.0f && isfinite(bp.inv_w) && isfinite(bp.c) && M <= kCondLimit * bp.W) ? 1 : 0;
-      bp.hb = (unsigned)(pl * HS * 4) - magic_bits * C4;
-      s_bp[pl] = bp;
+      const int fast = (W > 0.0f && isfinite(inv_w) && isfinite(c) && M <= kCondLimit * W) ? 1 : 0;
+      s_bpf[pl] = make_float4(mn, W, inv_w, c);
+      s_bpi[pl] = make_int4((int)((unsigned)((pl >> 1) * HS * 4) - magic_bits * C4), (int)(1u << (16 * (pl & 1))),
+                            fast, 0);
     }
+    __syncthreads();  // s_dk and s_rowfeat complete
+    for (int r = threadIdx.x; r < U && r < kStUMax; r += kStThreads) s_rowoff[r] = (int64_t)s_rowfeat[r] * ds.ld;
+    const int nslot = assign_snake(it.np, s_dk, s_kcnt, s_assign);
     const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
-    const int64_t len = it.end - it.beg;
     if (U <= kStUMax) {
-      const int St = choose_st<kStEpt>(U);
-      const int64_t ntile = (len + St - 1) / St;
-      TileLoader<kStEpt> ld;
-      bool vec = contig && len >= St;
-      ld.load(ds, idx, it.beg, it.end, St, U, s_rowfeat, vec);
-      for (int64_t tt = 0; tt < ntile; ++tt) {
-        __syncthreads();
-        ld.store(s_tile, St, U, vec);
-        if (threadIdx.x < St) {
-          // labels outside [0, C) and padding: a very negative offset that the
-          // unsigned clamp sends to the trash word
-          s_y4[threadIdx.x] = (ld.ylab >= 0 && ld.ylab < C) ? ld.ylab * 4 : (INT_MIN / 2);
+      // the item's labels as bytes (0xFF: padding or outside [0, C)); read
+      // after the first tile barrier
+      const int len = (int)(it.end - it.beg);
+      for (int e = threadIdx.x; e < len + 256; e += kStThreads) {
+        unsigned b = 0xFFu;
+        if (e < len) {
+          const unsigned y = ds.y[safe_sample(idx[it.beg + e], ds.n)];
+          b = y < (unsigned)C ? y : 0xFFu;
         }
-        __syncthreads();
-        if (tt + 1 < ntile) {
-          const int64_t nb = it.beg + (tt + 1) * St;
-          vec = contig && (it.end - nb) >= St;
-          ld.load(ds, idx, nb, min(it.end, nb + St), St, U, s_rowfeat, vec);
-        }
-        for (int pl = warp; pl < it.np; pl += kStWarps) {
-          const BinParams bp = s_bp[pl];
-          if (bp.fast)
-            hist_tile_k<KMAX>(s_dk[pl], s_tile, s_y4, s_drow + pl * KMAX, s_dsg + pl * KMAX, St, lane, bp, C4, limit,
-                              s_histb);
-          else
-            hist_tile_slow(s_dk[pl], s_tile, s_y4, s_drow + pl * KMAX, s_dsg + pl * KMAX, St, lane, bp, B, C, pl * HS,
-                           s_hist);
-        }
+        s_lab[e] = (uint8_t)b;
       }
+      if (St == 256)
+        hist_item<4, 2>(ds, idx, it, U, contig, s_tile, s_lab, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
+                     s_bpi, B, HS, C4, limit, s_hist, lane, warp);
+      else if (St == 128)
+        hist_item<4, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
+                     s_bpi, B, HS, C4, limit, s_hist, lane, warp);
+      else
+        hist_item<2, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
+                     s_bpi, B, HS, C4, limit, s_hist, lane, warp);
     } else {
       // direct path for wide groups (rare): one warp per projection, gathers
       for (int pl = warp; pl < it.np; pl += kStWarps) {
@@ -737,7 +882,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         const int rb = pv.beg[q];
         int k = pv.end[q] - rb;
         k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
-        const BinParams bp = s_bp[pl];
+        const float4 bf = s_bpf[pl];
+        const unsigned inc = 1u << (16 * (pl & 1));
         for (int64_t e = it.beg + lane; e < it.end; e += 32) {
           const int64_t s = safe_sample(idx[e], ds.n);
           float acc = 0.0f;
@@ -748,7 +894,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
             acc = __fadd_rn(acc, pv.sign[rb + jj] == 1 ? x : -x);
           }
           const int yv = ds.y[s];
-          if (yv < C) atomicAdd(&s_hist[pl * HS + bin_of(acc, bp.mn, bp.W, bp.inv_w, B) * C + yv], 1);
+          if (yv < C) atomicAdd(&s_hist[(pl >> 1) * HS + bin_of(acc, bf.x, bf.y, bf.z, B) * C + yv], inc);
         }
       }
     }
@@ -757,10 +903,11 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
     const int BC = B * C;
     for (int pl = warp; pl < it.np; pl += kStWarps) {
       int32_t* g = hist + (it.h * P + it.p0 + pl) * (int64_t)BC;
-      const int32_t* h = s_hist + pl * HS;
+      const uint32_t* h = s_hist + (pl >> 1) * HS;
+      const int sh = 16 * (pl & 1);
       for (int r = lane; r < BC; r += 32) {
-        int v = h[r];
-        if (r >= BC - C) v += h[r + C];
+        int v = (int)((h[r] >> sh) & 0xffffu);
+        if (r >= BC - C) v += (int)((h[r + C] >> sh) & 0xffffu);
         if (v) atomicAdd(&g[r], v);
       }
     }
@@ -769,22 +916,24 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
 
 // ---- host side ----------------------------------------------------------------
 int hist_group_size(int B, int C) {
-  // histogram shared memory <= 100 KB: PG * (B + 1) * C * 4
-  int pg = 32;
-  while (pg > 1 && (size_t)pg * (B + 1) * C * 4 > 100 * 1024) pg >>= 1;
-  return pg;
+  // 16-bit counters, two projections per word, in <= 100 KB of shared memory
+  const int pair_bytes = (B + 1) * C * 4;
+  int pg = 2 * ((100 * 1024) / pair_bytes);
+  return pg < 1 ? 1 : (pg > kHistPGMax ? kHistPGMax : pg);
 }
 
-size_t mm_smem_bytes(int d, int kmax) {
-  const int nw = (d + 31) >> 5;
-  return (size_t)kStThreads * kMmEpt * 4 + (size_t)kMmGroup * 32 * 8 + (size_t)nw * 8 + kStUMax * 4 +
-         kMmGroup * 4 + (size_t)kMmGroup * kmax * 6 + 64;
+// The feature bitmap (2 * ceil(d/32) words <= 16 KB) lives in the third tile
+// buffer, so d does not change the size.
+static_assert(kStMaxWords * 8 <= kTileF * 4, "bitmap must fit a tile buffer");
+size_t mm_smem_bytes(int /*d*/, int kmax) {
+  return (size_t)3 * kTileF * 4 + (size_t)kMmGroup * 32 * 8 + (size_t)kMmGroup * kmax * 4 + kMmGroup * 8 +
+         kStUMax * 12;
 }
-size_t hist_smem_bytes(int d, int kmax, int B, int C, int PG) {
-  const int nw = (d + 31) >> 5;
-  const size_t hist_words = ((size_t)PG * (B + 1) * C + 1 + 3) & ~(size_t)3;
-  return (size_t)kStThreads * kStEpt * 4 + 256 * 4 + hist_words * 4 + (size_t)nw * 8 + kStUMax * 4 + 32 * 4 +
-         (size_t)32 * kmax * 6 + 64;
+size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG) {
+  const int npair = (PG + 1) >> 1;
+  const size_t hist_words = ((size_t)npair * (B + 1) * C + 1 + 3) & ~(size_t)3;
+  return (size_t)3 * kTileF * 4 + kMaxItem + 256 + hist_words * 4 + (size_t)kHistPGMax * kmax * 4 +
+         kHistPGMax * 8 + kStUMax * 12;
 }
 
 bool staged_supported(int d) { return d <= kStMaxWords * 32; }
@@ -806,6 +955,11 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
   const DeviceInfo& di = device_info();
   const int P = a.pv.P, C = a.ds.C, B = a.B, d = a.ds.d;
   const int PG = hist_group_size(B, C);
+  // histogram items: at most kMaxItem samples (label bytes in shared memory,
+  // 16-bit counters); min / max items a quarter of that, so that a single
+  // large node still spreads over every SM
+  const int64_t S2 = S > kMaxItem ? kMaxItem : S;
+  const int64_t S1 = S2 / 4 > 1024 ? S2 / 4 : (S2 < 1024 ? S2 : 1024);
   cudaError_t e;
   {
     const size_t smem = (size_t)4 * (((d + 31) >> 5) + kStUMax) * 4;
@@ -817,20 +971,17 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
     k_groups<<<di.num_sms * 2, 128, smem, st>>>(plan_total, hist_nodes, a.pv, d, kMmUMax, kMmGroup, kStUMax, PG,
                                                 ss.ng1, ss.gs1, ss.ng2, ss.gs2);
   }
-  ItemScanF isf{plan_total, hist_nodes, a.node_off, ss.ng1, ss.ng2, S, ss.item_off1, ss.item_off2};
+  ItemScanF isf{plan_total, hist_nodes, a.node_off, ss.ng1, ss.ng2, S1, S2, ss.item_off1, ss.item_off2};
   e = run_scan(isf, m_hist_cap, ss.tiles, ss.item_total, st, "item_scan");
   if (e != cudaSuccess) return e;
-  StagedPlan sp1{plan_total, hist_nodes, a.node_off, ss.ng1, ss.gs1, ss.item_off1, ss.item_total, 0, S};
-  StagedPlan sp2{plan_total, hist_nodes, a.node_off, ss.ng2, ss.gs2, ss.item_off2, ss.item_total, 1, S};
+  StagedPlan sp1{plan_total, hist_nodes, a.node_off, ss.ng1, ss.gs1, ss.item_off1, ss.item_total, 0, S1};
+  StagedPlan sp2{plan_total, hist_nodes, a.node_off, ss.ng2, ss.gs2, ss.item_off2, ss.item_total, 1, S2};
   {
     const size_t smem = mm_smem_bytes(d, KMAX);
     e = cudaFuncSetAttribute(k_mm_staged<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mm_staged<KMAX>, kStThreads, smem);
-    if (occ < 1) occ = 1;
     ProfScope ps_("k_minmax", st);
-    k_mm_staged<KMAX><<<di.num_sms * occ, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp1, mm);
+    k_mm_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp1, mm);
   }
   {
     const size_t smem = hist_smem_bytes(d, KMAX, B, C, PG);
