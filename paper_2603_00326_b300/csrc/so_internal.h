@@ -15,6 +15,7 @@ constexpr int kMaxBins = 256;      // equal-width bins per projection
 constexpr int kMaxCap = 32;        // non-zeros per projection row
 constexpr int kMaxProj = 1024;     // projections per node
 constexpr int kMaxSortBelow = 2048;  // largest exact-path node + 1
+constexpr int kSortRegMax = 128;     // exact-path nodes sorted by one warp in registers
 
 // 4-lane int64 vector carried through the generic device scans.
 struct V4 {

@@ -101,8 +101,8 @@ struct PlanF {
   so_split* out;
   int64_t* left_counts;
 
-  // kind: 0 histogram, 1 exact path in registers (<= 512 samples),
-  // 2 exact path in shared memory (513 .. T-1 samples), 3 skip
+  // kind: 0 histogram, 1 exact path, one warp in registers (<= kSortRegMax
+  // samples), 2 exact path, one CTA in shared memory (up to T-1 samples), 3 skip
   // a node whose rows are malformed or whose segment leaves [0, n_total) is skipped
   __device__ bool is_bad(int64_t j) const {
     const int64_t b = off[j], e = off[j + 1];
@@ -112,7 +112,7 @@ struct PlanF {
     if (is_bad(j)) return 3;
     if (force_hist) return nv >= 1 ? 0 : 3;
     if (nv < 2) return 3;
-    if (!hist_only && nv < T) return nv <= 512 ? 1 : 2;
+    if (!hist_only && nv < T) return nv <= kSortRegMax ? 1 : 2;
     return 0;
   }
   __device__ V4 value(int64_t j) const {

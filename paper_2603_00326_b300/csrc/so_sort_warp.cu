@@ -1,14 +1,14 @@
 // so_sort_warp.cu -- exact path (Section 3.1: small nodes are split exactly by
-// sorting): one warp per (node, projection).
+// sorting).
 //
-// Pass 1: the warp gathers the node's projected values and sorts the
-// (order-preserving key, label) pairs -- in registers for nodes of up to 512
-// samples (bitonic network, lane-major layout e = lane*EPL + r), in the
-// warp's shared-memory buffer for 513..2047 samples -- forms class prefix
-// counts with a packed warp scan, evaluates the float Gini gain of every
-// boundary between distinct values, takes the projection's float maximum
-// M_p, re-scores in double every candidate within M_p(1-eps) and stores the
-// projection's lexicographic best (double gain, lowest position).
+// Pass 1, per (node, projection): gather the node's projected values and sort
+// the (order-preserving key, label) pairs -- one warp in registers for nodes
+// of up to kSortRegMax samples (bitonic network, lane-major layout
+// e = lane*EPL + r), one CTA in shared memory for larger exact-path nodes --
+// form class prefix counts with a packed scan, evaluate the float Gini gain of
+// every boundary between distinct values, take the projection's float
+// maximum M_p, re-score in double every candidate within M_p(1-eps) and store
+// the projection's lexicographic best (double gain, lowest position).
 // Pass 2 (k_sortw_select): one warp per node takes M = max_p M_p and the
 // lexicographic best (gain, projection, position) over the projections with
 // M_p >= M(1-eps).  The double winner of the node is always in its
@@ -106,15 +106,25 @@ __device__ __forceinline__ void load_sort(const DatasetView& ds, const int32_t* 
   float v[EPL];
 #pragma unroll
   for (int r = 0; r < EPL; ++r) v[r] = 0.0f;
-  for (int jj = 0; jj < kk; ++jj) {
-    const int f = __shfl_sync(0xffffffffu, fl, jj);
-    const int sg = __shfl_sync(0xffffffffu, sl, jj);
-    const float* col = ds.X + (int64_t)f * ds.ld;
+  // four terms' gathers in flight at a time, added in order
+  for (int j0 = 0; j0 < kk; j0 += 4) {
+    float x[4][EPL];
+    int sg[4];
 #pragma unroll
-    for (int r = 0; r < EPL; ++r) {
-      if (sid[r] >= 0) {
-        const float x = __ldg(col + sid[r]);
-        v[r] = __fadd_rn(v[r], sg == 1 ? x : -x);
+    for (int u = 0; u < 4; ++u) {
+      const int jj = j0 + u < kk ? j0 + u : j0;
+      const int f = __shfl_sync(0xffffffffu, fl, jj);
+      sg[u] = __shfl_sync(0xffffffffu, sl, jj);
+      const float* col = ds.X + (int64_t)f * ds.ld;
+#pragma unroll
+      for (int r = 0; r < EPL; ++r) x[u][r] = (j0 + u < kk && sid[r] >= 0) ? __ldg(col + sid[r]) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j0 + u < kk) {
+#pragma unroll
+        for (int r = 0; r < EPL; ++r)
+          if (sid[r] >= 0) v[r] = __fadd_rn(v[r], sg[u] == 1 ? x[u][r] : -x[u][r]);
       }
     }
   }
@@ -263,96 +273,12 @@ __device__ __forceinline__ void proj_pass1_reg(const DatasetView& ds, const int3
   score_projection(nc, ds.C, eps, lane, [&](auto visit) { scan_candidates<EPL>(k, nc, ds.C, lane, visit); }, out);
 }
 
-// Shared-memory form for 513..2047 samples: the warp's buffer holds NP keys.
-__device__ __forceinline__ void proj_pass1_smem(const DatasetView& ds, const int32_t* idx, const ProjView& pv,
-                                                int64_t q, const SortNodeCtx& nc, int lane, float eps,
-                                                unsigned long long* buf, SortRes* out) {
-  int NP = 1024;
-  while (NP < nc.nv) NP <<= 1;
-  const int rb = pv.beg[q];
-  int kk = pv.end[q] - rb;
-  kk = kk < 0 ? 0 : (kk > kMaxCap ? kMaxCap : kk);
-  int fl = 0, sl = 1;
-  if (lane < kk) {
-    fl = pv.feat[rb + lane];
-    fl = (fl < 0 || fl >= ds.d) ? 0 : fl;
-    sl = pv.sign[rb + lane];
-  }
-  for (int e0 = 0; e0 < NP; e0 += 32) {
-    // all lanes take part (the shuffles need a converged warp); positions
-    // past the node compute on its first sample and store a padding key
-    const int e = e0 + lane;
-    const bool live = e < nc.nv;
-    const int64_t sid = safe_sample(idx[nc.beg + (live ? e : 0)], ds.n);
-    float v = 0.0f;
-    for (int jj = 0; jj < kk; ++jj) {
-      const int f = __shfl_sync(0xffffffffu, fl, jj);
-      const int sg = __shfl_sync(0xffffffffu, sl, jj);
-      const float x = __ldg(ds.X + (int64_t)f * ds.ld + sid);
-      v = __fadd_rn(v, sg == 1 ? x : -x);
-    }
-    buf[e] = live ? (((unsigned long long)f2key(v) << 32) | (unsigned long long)(unsigned)ds.y[sid]) : ~0ull;
-  }
-  __syncwarp();
-  for (int size = 2; size <= NP; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = lane; i < NP / 2; i += 32) {
-        const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool up = (lo & size) == 0;
-        const unsigned long long a = buf[lo], b = buf[hi];
-        if ((a > b) == up) {
-          buf[lo] = b;
-          buf[hi] = a;
-        }
-      }
-      __syncwarp();
-    }
-  }
-  // lane owns positions [lane*E, lane*E + E)
-  const int E = NP / 32;
-  const int i0 = lane * E;
-  auto walk = [&](auto visit) {
-    PackedCnt own{0, 0};
-    for (int e = 0; e < E; ++e)
-      if (i0 + e < nc.nv) pc_add(own, (int)(buf[i0 + e] & 0xFFull));
-    unsigned long long ilo = own.lo, ihi = own.hi;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long ul = __shfl_up_sync(0xffffffffu, ilo, o);
-      const unsigned long long uh = __shfl_up_sync(0xffffffffu, ihi, o);
-      if (lane >= o) {
-        ilo += ul;
-        ihi += uh;
-      }
-    }
-    PackedCnt run{ilo - own.lo, ihi - own.hi};
-    for (int e = 0; e < E; ++e) {
-      const int i = i0 + e;
-      if (i >= nc.nv - 1) break;
-      const unsigned long long x = buf[i];
-      pc_add(run, (int)(x & 0xFFull));
-      const unsigned a = (unsigned)(x >> 32), b = (unsigned)(buf[i + 1] >> 32);
-      if (a != b) {
-        int L[kMaxClasses];
-#pragma unroll
-        for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
-        visit(i, run, gain32(L, nc.N, ds.C, nc.nv, i + 1), a, b);
-      }
-    }
-  };
-  score_projection(nc, ds.C, eps, lane, walk, out);
-  __syncwarp();
-}
-
-__device__ __forceinline__ int epl_of(int nv) {
-  return nv <= 32 ? 1 : nv <= 64 ? 2 : nv <= 128 ? 4 : nv <= 256 ? 8 : 16;
-}
+__device__ __forceinline__ int epl_of(int nv) { return nv <= 32 ? 1 : nv <= 64 ? 2 : 4; }
 
 }  // namespace
 
-// Pass 1, register form: one warp per (node of <= 512 samples, projection).
-__global__ void __launch_bounds__(256, 2) k_sortw_scan(DatasetView ds, const int32_t* __restrict__ idx,
+// Pass 1, register form: one warp per (node of <= kSortRegMax samples, projection).
+__global__ void __launch_bounds__(256, 4) k_sortw_scan(DatasetView ds, const int32_t* __restrict__ idx,
                                                        const int64_t* __restrict__ off, ProjView pv,
                                                        const V4* plan_total, const int32_t* nodes,
                                                        const int32_t* __restrict__ node_cls, float eps,
@@ -373,35 +299,211 @@ __global__ void __launch_bounds__(256, 2) k_sortw_scan(DatasetView ds, const int
     switch (epl_of(nc.nv)) {
       case 1: proj_pass1_reg<1>(ds, idx, pv, q, nc, lane, eps, out); break;
       case 2: proj_pass1_reg<2>(ds, idx, pv, q, nc, lane, eps, out); break;
-      case 4: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, eps, out); break;
-      case 8: proj_pass1_reg<8>(ds, idx, pv, q, nc, lane, eps, out); break;
-      default: proj_pass1_reg<16>(ds, idx, pv, q, nc, lane, eps, out); break;
+      default: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, eps, out); break;
     }
   }
 }
 
-// Pass 1, shared-memory form: one warp per (node of 513..2047 samples, projection).
-constexpr int kSwSmemWarps = 4;
-__global__ void __launch_bounds__(kSwSmemWarps * 32) k_sortw_scan_smem(DatasetView ds, const int32_t* __restrict__ idx,
-                                                                      const int64_t* __restrict__ off, ProjView pv,
-                                                                      const V4* plan_total, const int32_t* nodes,
-                                                                      const int32_t* __restrict__ node_cls,
-                                                                      int NPmax, float eps, SortRes* res) {
-  extern __shared__ unsigned long long s_keys[];
+// Pass 1, CTA form: one CTA of kScThreads per (node of kSortRegMax+1 .. T-1
+// samples, projection).  The node's projected values are gathered by the
+// whole CTA (each thread up to NP/kScThreads samples, the projection's terms
+// four at a time), sorted as (key, label) pairs with a shared-memory bitonic
+// network, and scanned in per-thread chunks of consecutive sorted positions
+// with a block-wide exclusive scan of the packed class counters.
+constexpr int kScThreads = 128;
+constexpr int kScWarps = kScThreads / 32;
+
+struct ScShared {
+  int feat[kMaxCap];
+  int sign[kMaxCap];
+  unsigned long long wlo[kScWarps], whi[kScWarps];
+  float wmax[kScWarps];
+  Best wbest[kScWarps];
+};
+
+__device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* __restrict__ idx, const SortNodeCtx& nc,
+                                          int NP, int kk, const ScShared& sh, unsigned long long* keys) {
+  constexpr int kPer = 4;  // samples per thread per round, loads of 4 terms in flight per sample
+  for (int e0 = threadIdx.x; e0 < NP; e0 += kScThreads * kPer) {
+    int64_t sid[kPer];
+    float v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = e0 + u * kScThreads;
+      sid[u] = e < nc.nv ? safe_sample(idx[nc.beg + e], ds.n) : -1;
+      v[u] = 0.0f;
+    }
+    for (int j0 = 0; j0 < kk; j0 += 4) {
+      float x[4][kPer];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float* col = ds.X + (int64_t)sh.feat[j0 + jj < kk ? j0 + jj : j0] * ds.ld;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) x[jj][u] = (j0 + jj < kk && sid[u] >= 0) ? __ldg(col + sid[u]) : 0.0f;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        if (j0 + jj < kk) {
+          const bool pos = sh.sign[j0 + jj] == 1;
+#pragma unroll
+          for (int u = 0; u < kPer; ++u) v[u] = __fadd_rn(v[u], pos ? x[jj][u] : -x[jj][u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = e0 + u * kScThreads;
+      if (e < NP)
+        keys[e] = sid[u] >= 0 ? (((unsigned long long)f2key(v[u]) << 32) | (unsigned long long)(unsigned)ds.y[sid[u]])
+                              : ~0ull;
+    }
+  }
+}
+
+__device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP) {
+  for (int size = 2; size <= NP; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < NP / 2; i += kScThreads) {
+        const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const unsigned long long a = keys[lo], b = keys[hi];
+        if ((a > b) == up) {
+          keys[lo] = b;
+          keys[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Walks this thread's chunk [i0, i0+E) of sorted positions; calls
+// visit(i, run, g32, a, b) for each candidate (boundary between distinct
+// values), run = packed class counts of positions 0..i.
+template <class Visit>
+__device__ __forceinline__ void sc_walk(const unsigned long long* keys, const SortNodeCtx& nc, int C, int i0, int E,
+                                        PackedCnt run, Visit visit) {
+  for (int e = 0; e < E; ++e) {
+    const int i = i0 + e;
+    if (i >= nc.nv - 1) break;
+    const unsigned long long x = keys[i];
+    pc_add(run, (int)(x & 0xFFull));
+    const unsigned a = (unsigned)(x >> 32), b = (unsigned)(keys[i + 1] >> 32);
+    if (a != b) {
+      int L[kMaxClasses];
+#pragma unroll
+      for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
+      visit(i, run, gain32(L, nc.N, C, nc.nv, i + 1), a, b);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const int32_t* __restrict__ idx,
+                                                          const int64_t* __restrict__ off, ProjView pv,
+                                                          const V4* plan_total, const int32_t* nodes,
+                                                          const int32_t* __restrict__ node_cls, float eps,
+                                                          SortRes* res) {
+  extern __shared__ unsigned long long s_keys[];  // [NP <= kMaxSortBelow]
+  __shared__ ScShared sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long* buf = s_keys + (int64_t)warp * NPmax;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int P = pv.P;
   const int64_t total = plan_total->w * P;
-  for (int64_t t = gw; t < total; t += nw) {
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
     const int64_t s = t / P;
     const int p = (int)(t - s * P);
     SortNodeCtx nc;
     int j;
     node_ctx(off, nodes, s, node_cls, nc, j);
     const int64_t q = (int64_t)j * P + p;
-    proj_pass1_smem(ds, idx, pv, q, nc, lane, eps, buf, res + q);
+    int NP = 2 * kScThreads;
+    while (NP < nc.nv) NP <<= 1;
+    const int rb = pv.beg[q];
+    int kk = pv.end[q] - rb;
+    kk = kk < 0 ? 0 : (kk > kMaxCap ? kMaxCap : kk);
+    __syncthreads();  // previous (node, projection) done with shared memory
+    if (threadIdx.x < kk) {
+      int f = pv.feat[rb + threadIdx.x];
+      sh.feat[threadIdx.x] = (f < 0 || f >= ds.d) ? 0 : f;
+      sh.sign[threadIdx.x] = pv.sign[rb + threadIdx.x];
+    }
+    __syncthreads();
+    sc_gather(ds, idx, nc, NP, kk, sh, s_keys);
+    __syncthreads();
+    sc_bitonic(s_keys, NP);
+    // this thread's chunk of consecutive sorted positions and its left counts
+    const int E = NP / kScThreads;
+    const int i0 = threadIdx.x * E;
+    PackedCnt own{0, 0};
+    for (int e = 0; e < E; ++e)
+      if (i0 + e < nc.nv) pc_add(own, (int)(s_keys[i0 + e] & 0xFFull));
+    unsigned long long ilo = own.lo, ihi = own.hi;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long ul = __shfl_up_sync(0xffffffffu, ilo, o);
+      const unsigned long long uh = __shfl_up_sync(0xffffffffu, ihi, o);
+      if (lane >= o) {
+        ilo += ul;
+        ihi += uh;
+      }
+    }
+    if (lane == 31) {
+      sh.wlo[warp] = ilo;
+      sh.whi[warp] = ihi;
+    }
+    __syncthreads();
+    PackedCnt run{ilo - own.lo, ihi - own.hi};
+    for (int w = 0; w < warp; ++w) {
+      run.lo += sh.wlo[w];
+      run.hi += sh.whi[w];
+    }
+    // float maximum of the projection
+    float m = -1.0f;
+    sc_walk(s_keys, nc, ds.C, i0, E, run, [&](int, const PackedCnt&, float g, unsigned, unsigned) { m = fmaxf(m, g); });
+    m = warp_max(m);
+    if (lane == 0) sh.wmax[warp] = m;
+    __syncthreads();
+    m = sh.wmax[0];
+    for (int w = 1; w < kScWarps; ++w) m = fmaxf(m, sh.wmax[w]);
+    // double re-score of the candidates within m(1-eps); lexicographic best
+    Best lb;
+    lb.c = Cand{-1.0, INT_MAX, INT_MAX};
+    lb.ka = lb.kb = 0u;
+    lb.L = PackedCnt{0, 0};
+    if (m > 0.0f) {
+      const float thr = __fmul_rn(m, 1.0f - eps);
+      sc_walk(s_keys, nc, ds.C, i0, E, run, [&](int i, const PackedCnt& r, float g, unsigned a, unsigned b) {
+        if (g >= thr) {
+          int L[kMaxClasses];
+#pragma unroll
+          for (int cc = 0; cc < kMaxClasses; ++cc) L[cc] = pc_get(r, cc);
+          const Cand c{gain64(L, nc.N, ds.C, nc.nv, i + 1), 0, i};
+          if (better(c, lb.c)) {
+            lb.c = c;
+            lb.ka = a;
+            lb.kb = b;
+            lb.L = r;
+          }
+        }
+      });
+    }
+    best_reduce(lb);
+    if (lane == 0) sh.wbest[warp] = lb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Best b = sh.wbest[0];
+      for (int w = 1; w < kScWarps; ++w)
+        if (better(sh.wbest[w].c, b.c)) b = sh.wbest[w];
+      SortRes r;
+      r.m32 = m;
+      r.g64 = b.c.g;
+      r.cand = b.c.cand;
+      r.ka = b.ka;
+      r.kb = b.kb;
+      r.llo = b.L.lo;
+      r.lhi = b.L.hi;
+      res[q] = r;
+    }
   }
 }
 
@@ -502,18 +604,13 @@ cudaError_t launch_sort_warp(const SearchArgs& a, const V4* plan_total, const in
     k_sortw_scan<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, tiny, node_cls, a.eps,
                                                  res);
   }
-  if (!a.hist_only && a.T > 513) {
-    int NPmax = 1024;
+  if (!a.hist_only && a.T > kSortRegMax + 1) {
+    int NPmax = 2 * kScThreads;
     while (NPmax < a.T - 1) NPmax <<= 1;
-    const size_t smem = (size_t)kSwSmemWarps * NPmax * 8;
-    cudaError_t e = cudaFuncSetAttribute(k_sortw_scan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sortw_scan_smem, kSwSmemWarps * 32, smem);
-    if (occ < 1) occ = 1;
-    ProfScope ps_("k_sortw_scan_smem", st);
-    k_sortw_scan_smem<<<di.num_sms * occ, kSwSmemWarps * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total,
-                                                                         med, node_cls, NPmax, a.eps, res);
+    const size_t smem = (size_t)NPmax * 8;
+    ProfScope ps_("k_sortc_scan", st);
+    k_sortc_scan<<<di.num_sms * 16, kScThreads, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, med, node_cls,
+                                                           a.eps, res);
   }
   {
     ProfScope ps_("k_sortw_select", st);

@@ -159,6 +159,9 @@ def _single_cases():
         dict(n=900, hist_only=False, T=1024),      # medium exact path
         dict(n=20, hist_only=False, T=1024),       # tiny exact path
         dict(n=33, hist_only=False, T=1024),
+        dict(n=128, hist_only=False, T=1024),      # largest register-sorted node
+        dict(n=129, hist_only=False, T=1024),      # smallest CTA-sorted node
+        dict(n=257, hist_only=False, T=1024),
         dict(n=1, hist_only=False, T=1024),
         dict(n=2, hist_only=True, T=0),
         dict(n=2047, hist_only=False, T=2048),     # largest exact node
