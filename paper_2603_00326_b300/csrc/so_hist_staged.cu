@@ -568,7 +568,7 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
                                         int U, bool contig, float* s_tile, const int* s_rowfeat,
                                         const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk,
                                         const uint32_t* s_dpk, int kmax, float* s_pmin, float* s_pmax, int lane,
-                                        int warp) {
+                                        int warp, float* vbuf, int64_t n_total) {
   constexpr int St = 32 * V * NQ;
   const int ntile = (int)((it.end - it.beg + St - 1) / St);
   const int* my = s_assign + warp * nslot;
@@ -603,6 +603,19 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
         mn = fminf(mn, acc[i]);
         mx = fmaxf(mx, acc[i]);
       }
+      if (vbuf) {
+        // keep the values for the histogram pass (positions of this node only)
+        const int64_t t0 = it.beg + (int64_t)tt * St;
+        float* vp = vbuf + (int64_t)(it.p0 + pl) * n_total + t0;
+        const int64_t rem = it.end - t0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int u = 0; u < V; ++u) {
+            const int e = 32 * V * q + V * lane + u;
+            if (e < rem) vp[e] = acc[V * q + u];
+          }
+      }
       s_pmin[pl * 32 + lane] = mn;
       s_pmax[pl * 32 + lane] = mx;
     }
@@ -611,7 +624,8 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
 
 template <int KMAX>
 __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, const int32_t* __restrict__ idx,
-                                                            ProjView pv, StagedPlan sp, uint32_t* mm) {
+                                                            ProjView pv, StagedPlan sp, uint32_t* mm, float* vbuf,
+                                                            int64_t n_total) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
   float* s_tile = reinterpret_cast<float*>(s_raw);                         // [3][kTileF]
@@ -645,13 +659,13 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
     if (U <= kMmUMax) {
       if (St == 256)
         mm_item<4, 2>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
-                   lane, warp);
+                   lane, warp, vbuf, n_total);
       else if (St == 128)
         mm_item<4, 1>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
-                   lane, warp);
+                   lane, warp, vbuf, n_total);
       else
         mm_item<2, 1>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
-                   lane, warp);
+                   lane, warp, vbuf, n_total);
     } else {
       // direct path for wide groups: each warp gathers its projections' features
       for (int pl = warp; pl < it.np; pl += kStWarps) {
@@ -671,6 +685,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
           }
           mn = fminf(mn, acc);
           mx = fmaxf(mx, acc);
+          if (vbuf) vbuf[(int64_t)(it.p0 + pl) * n_total + e] = acc;
         }
         s_pmin[pl * 32 + lane] = mn;
         s_pmax[pl * 32 + lane] = mx;
@@ -793,10 +808,63 @@ __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* 
   }
 }
 
+// The item's histograms from projected values kept by the min / max pass (the
+// node's samples are gathered, so reading 4 bytes per sample-projection beats
+// gathering the feature columns again).  No tiles and no barriers: each warp
+// streams its assigned projections over the item, four samples per lane and
+// four steps in flight.
+__device__ __forceinline__ void hist_item_buf(const float* __restrict__ vbuf, int64_t n_total, const ItemPos& it,
+                                              unsigned lab_base, const int* s_assign, int nslot,
+                                              const float4* s_bpf, const int4* s_bpi, int B, int C, int HS,
+                                              unsigned C4, unsigned limit_abs, uint32_t* s_hist, int lane,
+                                              int warp) {
+  const int len = (int)(it.end - it.beg);
+  for (int sl = 0; sl < nslot; ++sl) {
+    const int pl = s_assign[warp * nslot + sl];
+    if (pl < 0) break;
+    const float4 bf = s_bpf[pl];
+    const int4 bi = s_bpi[pl];
+    const BinParams bp{bf.x, bf.y, bf.z, bf.w, su32(s_hist) + (unsigned)bi.x, (unsigned)bi.y, bi.z};
+    const float* vp = vbuf + (int64_t)(it.p0 + pl) * n_total + it.beg;
+    for (int e0 = 0; e0 < len; e0 += 512) {
+      float v[16];
+      int yo[16];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int e = e0 + 128 * u + 4 * lane + w;
+          v[4 * u + w] = e < len ? __ldg(vp + e) : __int_as_float(0x7fc00000);
+        }
+        const unsigned lw = lds_u32(lab_base + (unsigned)(e0 + 128 * u + 4 * lane));
+#pragma unroll
+        for (int w = 0; w < 4; ++w) yo[4 * u + w] = label_off8((lw >> (8 * w)) & 0xffu);
+      }
+      if (bp.fast) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float tq = __fadd_rn(__fmaf_rn(v[i], bp.inv_w, bp.c), kMagic);
+          const float q1 = __fadd_rn(tq, 1.0f - kMagic);
+          const float tb = __fadd_rn(bp.mn, __fmul_rn(q1, bp.W));
+          unsigned a = __float_as_uint(tq) * C4 + (bp.hb + (unsigned)yo[i]);
+          if (tb <= v[i]) a += C4;
+          reds_add(min(a, limit_abs), bp.inc);
+        }
+      } else {
+        const int wbase = (pl >> 1) * HS;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (yo[i] >= 0) atomicAdd(&s_hist[wbase + bin_of(v[i], bp.mn, bp.W, bp.inv_w, B) * C + (yo[i] >> 2)], bp.inc);
+      }
+    }
+  }
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, const int32_t* __restrict__ idx,
                                                               ProjView pv, StagedPlan sp, int B, int PG,
-                                                              const uint32_t* __restrict__ mm, int32_t* hist) {
+                                                              const uint32_t* __restrict__ mm, int32_t* hist,
+                                                              const float* __restrict__ vbuf, int64_t n_total) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
   const int C = ds.C;
@@ -805,8 +873,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   const int hist_words = (npair * HS + 1 + 3) & ~3;
   // every region starts on a 16-byte boundary
   float* s_tile = reinterpret_cast<float*>(s_raw);                           // [3][kTileF]
-  uint8_t* s_lab = reinterpret_cast<uint8_t*>(s_tile + 3 * kTileF);          // [kMaxItem + 256] item labels
-  uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_lab + kMaxItem + 256);    // [hist_words]
+  uint8_t* s_lab = reinterpret_cast<uint8_t*>(s_tile + 3 * kTileF);          // [kMaxItem + 512] item labels
+  uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_lab + kMaxItem + 512);    // [hist_words]
   uint32_t* s_dpk = s_hist + hist_words;                                     // [kHistPGMax*KMAX]
   int* s_dk = reinterpret_cast<int*>(s_dpk + kHistPGMax * KMAX);             // [kHistPGMax]
   int* s_assign = s_dk + kHistPGMax;                                         // [kHistPGMax]
@@ -834,9 +902,14 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
       int4* h4 = reinterpret_cast<int4*>(s_hist);
       for (int e = threadIdx.x; e < hist_words / 4; e += kStThreads) h4[e] = make_int4(0, 0, 0, 0);
     }
-    const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
-    const int St = choose_st(U);
-    build_desc<KMAX>(pv, qbase, it.np, ds.d, St, s_bits, s_wpre, s_dk, s_dpk);
+    int U = 0, St = 64;
+    if (!vbuf) {
+      U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
+      St = choose_st(U);
+      build_desc<KMAX>(pv, qbase, it.np, ds.d, St, s_bits, s_wpre, s_dk, s_dpk);
+    } else if (threadIdx.x < it.np) {
+      s_dk[threadIdx.x] = 1;  // every projection costs the same when its values are read back
+    }
     if (threadIdx.x < it.np) {
       const int pl = threadIdx.x;
       const float mn = key2f(mm[(it.h * P + it.p0 + pl) * 2]);
@@ -853,12 +926,12 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
     __syncthreads();  // s_dk and s_rowfeat complete
     for (int r = threadIdx.x; r < U && r < kStUMax; r += kStThreads) s_rowoff[r] = (int64_t)s_rowfeat[r] * ds.ld;
     const int nslot = assign_snake(it.np, s_dk, s_kcnt, s_assign);
-    const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
-    if (U <= kStUMax) {
+    const bool contig = vbuf ? false : item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
+    if (vbuf || U <= kStUMax) {
       // the item's labels as bytes (0xFF: padding or outside [0, C)); read
       // after the first tile barrier
       const int len = (int)(it.end - it.beg);
-      for (int e = threadIdx.x; e < len + 256; e += kStThreads) {
+      for (int e = threadIdx.x; e < len + 512; e += kStThreads) {
         unsigned b = 0xFFu;
         if (e < len) {
           const unsigned y = ds.y[safe_sample(idx[it.beg + e], ds.n)];
@@ -866,7 +939,11 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         }
         s_lab[e] = (uint8_t)b;
       }
-      if (St == 256)
+      if (vbuf) {
+        __syncthreads();  // labels and warp assignment visible
+        hist_item_buf(vbuf, n_total, it, su32(s_lab), s_assign, nslot, s_bpf, s_bpi, B, C, HS, C4,
+                      su32(s_hist) + limit, s_hist, lane, warp);
+      } else if (St == 256)
         hist_item<4, 2>(ds, idx, it, U, contig, s_tile, s_lab, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
                      s_bpi, B, HS, C4, limit, s_hist, lane, warp);
       else if (St == 128)
@@ -932,7 +1009,7 @@ size_t mm_smem_bytes(int /*d*/, int kmax) {
 size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG) {
   const int npair = (PG + 1) >> 1;
   const size_t hist_words = ((size_t)npair * (B + 1) * C + 1 + 3) & ~(size_t)3;
-  return (size_t)3 * kTileF * 4 + kMaxItem + 256 + hist_words * 4 + (size_t)kHistPGMax * kmax * 4 +
+  return (size_t)3 * kTileF * 4 + kMaxItem + 512 + hist_words * 4 + (size_t)kHistPGMax * kmax * 4 +
          kHistPGMax * 8 + kStUMax * 12;
 }
 
@@ -981,14 +1058,15 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
     e = cudaFuncSetAttribute(k_mm_staged<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ProfScope ps_("k_minmax", st);
-    k_mm_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp1, mm);
+    k_mm_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp1, mm, a.vbuf, a.n_total);
   }
   {
     const size_t smem = hist_smem_bytes(d, KMAX, B, C, PG);
     e = cudaFuncSetAttribute(k_hist_staged<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ProfScope ps_("k_hist", st);
-    k_hist_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp2, B, PG, mm, hist);
+    k_hist_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp2, B, PG, mm, hist, a.vbuf,
+                                                              a.n_total);
   }
   return cudaGetLastError();
 }

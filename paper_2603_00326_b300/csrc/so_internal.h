@@ -86,6 +86,10 @@ struct SearchArgs {
   int32_t* hist_out = nullptr;
   float* gain32_out = nullptr;
   HistTuning tune{};
+  // optional [P][n_total] buffer: the min / max pass stores every
+  // histogram-path sample's projected values and the histogram pass reads
+  // them back instead of gathering the feature columns again
+  float* vbuf = nullptr;
 };
 
 // Scratch of the staged-tile histogram kernels (so_hist_staged.cu).
