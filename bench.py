@@ -225,12 +225,30 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1):
         F.train_forest(F.ForestConfig(n_trees=1, n_proj=8, lam=1.5, cap=8), dd)  # warm-up
         torch.cuda.synchronize()
         trees, secs = F.train_forest(cfg, dd)
+        # inference: every sample through every trained tree, and each tree's
+        # out-of-bag accuracy (samples its bootstrap never drew)
+        fo = S.upload_forest(trees, 2)
+        S.so_predict(dd.X, fo)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.so_predict(dd.X, fo)
+        torch.cuda.synchronize()
+        pred_s = time.perf_counter() - t0
+        oob_acc = []
+        for t, tr in enumerate(trees):
+            inbag = np.zeros(fs.n, bool)
+            inbag[F.root_indices(fs.n, t, cfg)] = True
+            p1, _ = S.so_predict(dd.X, S.upload_forest([tr], 2))
+            oob = ~inbag
+            oob_acc.append(float((p1.cpu().numpy()[oob] == fs.y[oob]).mean()))
         out["forest_2m"] = {"trees": forest_trees, "of": fp["n_trees"], "train_s": secs,
                             "s_per_tree": secs / forest_trees,
                             "projected_forest_s": secs / forest_trees * fp["n_trees"],
                             "mean_nodes": float(np.mean([t.n_nodes for t in trees])),
-                            "max_depth": int(max(int(t.depth.max()) for t in trees))}
-        del dd, trees
+                            "max_depth": int(max(int(t.depth.max()) for t in trees)),
+                            "predict_sample_trees_per_s": fs.n * forest_trees / pred_s,
+                            "oob_accuracy_per_tree": oob_acc}
+        del dd, trees, fo
     if wide_trees > 0 and only in (None, "wide"):
         # wide count-like data: n=500k, d=4096, 90% zeros, 5 classes, grown to purity
         ws_np = G.wide_counts()

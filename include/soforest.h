@@ -266,6 +266,36 @@ so_status so_train_tree(const so_dataset *ds, const int32_t *root_idx, int64_t n
 
 void so_tree_free(so_tree *tree);
 
+/* ---- forest inference ----------------------------------------------------
+ * A forest on the device: the trees' node arrays concatenated, tree t owning
+ * nodes [tree_off[t], tree_off[t+1]); child ids are local to their tree (as
+ * in so_tree), -1 for a leaf.  All arrays device, caller-owned:
+ *  tree_off [n_trees+1] int64; left, right, leaf_class, proj_nnz [n_nodes]
+ *  int32; feat [n_nodes*cap] int32 and sign [n_nodes*cap] int8 (a node's
+ *  projection, ascending features); threshold [n_nodes] float. */
+typedef struct {
+    int32_t n_trees;
+    int32_t n_classes;     /* 1..8 */
+    int32_t cap;           /* slots per node in feat/sign, 1..32 */
+    const int64_t *tree_off;
+    const int32_t *left, *right, *leaf_class, *proj_nnz, *feat;
+    const int8_t *sign;
+    const float *threshold;
+} so_forest;
+
+/* Forest prediction (the forest's use, Section 4's accuracy evaluation):
+ * every tree routes sample i from its root -- at an internal node the
+ * projection value of Section 3 step 1 (float, +0 start, ascending features,
+ * one rounding per term) goes left iff it is below the threshold -- and votes
+ * its leaf's class.  votes: device [n*n_classes] int32 or NULL; pred: device
+ * [n] int32, the class with most votes (ties to the lowest id).
+ * X: device, column-major X[f*ld + i], i < n, f < d; every feature id in the
+ * forest must be < d (checked on the device: a node with a bad feature or a
+ * child outside its tree makes the call return SO_EINTERNAL).  A route
+ * longer than 2^20 nodes stops (SO_EINTERNAL).  Synchronises `stream`. */
+so_status so_predict(const float *X, int64_t n, int32_t d, int64_t ld, const so_forest *forest,
+                     int32_t *votes, int32_t *pred, void *stream);
+
 /* The start-up crossover microbenchmark of Section 3.1: on this GPU, for node
  * sizes s = 32 .. 2047, times one batched split search of many s-sample nodes
  * drawn from ds on the exact path and on the histogram path (n_proj sampled

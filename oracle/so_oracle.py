@@ -308,3 +308,32 @@ def predict_tree(tree: Tree, X: np.ndarray, rows: np.ndarray) -> np.ndarray:
             node = tree.left[node] if acc < tree.threshold[node] else tree.right[node]
         out[r_i] = tree.leaf_class[node]
     return out
+
+
+def predict_tree_c(tree: Tree, X: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """Leaf class of each row through the C traversal (orc_predict_tree)."""
+    X = _c(X, np.float32)
+    rows = _c(rows, np.int32)
+    keep = {f: np.ascontiguousarray(getattr(tree, f)) for f in Tree.FIELDS}
+    t = OrcTree()
+    t.n_nodes = tree.n_nodes
+    t.n_classes = keep["class_counts"].shape[1] if keep["class_counts"].ndim == 2 else 1
+    t.cap = keep["feat"].shape[1]
+    for f, ct in (("left", C.c_int32), ("right", C.c_int32), ("depth", C.c_int32), ("leaf_class", C.c_int32),
+                  ("proj_nnz", C.c_int32), ("feat", C.c_int32), ("cand", C.c_int32), ("sign", C.c_int8),
+                  ("path", C.c_int8), ("threshold", C.c_float), ("n_samples", C.c_int64),
+                  ("class_counts", C.c_int64), ("gain", C.c_double)):
+        setattr(t, f, keep[f].ctypes.data_as(C.POINTER(ct)))
+    out = np.empty(rows.shape[0], dtype=np.int32)
+    lib().orc_predict_tree(C.byref(t), _p(X), X.shape[1], _p(rows), rows.shape[0], _p(out))
+    return out
+
+
+def predict_forest(trees, X: np.ndarray, rows: np.ndarray, n_classes: int):
+    """Majority vote of the trees' leaf classes; ties go to the lowest class.
+    Returns (pred int32 [n], votes int32 [n, n_classes])."""
+    votes = np.zeros((rows.shape[0], n_classes), dtype=np.int32)
+    for t in trees:
+        cls = predict_tree_c(t, X, rows)
+        np.add.at(votes, (np.arange(rows.shape[0]), cls), 1)
+    return np.argmax(votes, axis=1).astype(np.int32), votes

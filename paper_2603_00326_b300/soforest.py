@@ -9,7 +9,7 @@ from __future__ import annotations
 import ctypes as C
 import dataclasses
 import os
-from typing import Optional
+from typing import List, Optional
 
 import numpy as np
 
@@ -65,6 +65,13 @@ class so_tree(C.Structure):
                 ("gain", C.POINTER(C.c_double))]
 
 
+class so_forest(C.Structure):
+    _fields_ = [("n_trees", C.c_int32), ("n_classes", C.c_int32), ("cap", C.c_int32),
+                ("tree_off", C.c_void_p), ("left", C.c_void_p), ("right", C.c_void_p),
+                ("leaf_class", C.c_void_p), ("proj_nnz", C.c_void_p), ("feat", C.c_void_p),
+                ("sign", C.c_void_p), ("threshold", C.c_void_p)]
+
+
 class so_profile_entry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -96,6 +103,7 @@ _SIGS = {
                              C.POINTER(so_tree), _V]),
     "so_tree_free": (None, [C.POINTER(so_tree)]),
     "so_autotune": (_I32, [C.POINTER(so_dataset), _I32, _D, _I32, C.POINTER(so_split_params), _V, _V, _V, _V]),
+    "so_predict": (_I32, [_V, _I64, _I32, _I64, C.POINTER(so_forest), _V, _V, _V]),
     "so_last_error": (C.c_char_p, []),
     "so_shutdown": (None, []),
     "so_version": (C.c_char_p, []),
@@ -349,6 +357,62 @@ def so_train_tree(ds: DeviceDataset, root_idx, params: so_tree_params, stream=No
             gain=arr(t.gain, m, np.float64))
     finally:
         lib().so_tree_free(C.byref(t))
+
+
+@dataclasses.dataclass
+class DeviceForest:
+    """Trees' node arrays concatenated on the device (see so_forest)."""
+    n_trees: int
+    n_classes: int
+    cap: int
+    arrays: dict
+
+    def c(self) -> so_forest:
+        a = self.arrays
+        return so_forest(self.n_trees, self.n_classes, self.cap, a["tree_off"].data_ptr(), a["left"].data_ptr(),
+                         a["right"].data_ptr(), a["leaf_class"].data_ptr(), a["proj_nnz"].data_ptr(),
+                         a["feat"].data_ptr(), a["sign"].data_ptr(), a["threshold"].data_ptr())
+
+
+def upload_forest(trees: List[Tree], n_classes: int, device="cuda") -> DeviceForest:
+    """Concatenates host trees (so_train_tree results) into a DeviceForest."""
+    import torch
+    cap = max(int(t.feat.shape[1]) for t in trees) if trees else 1
+    sizes = [int(t.n_nodes) for t in trees]
+    off = np.zeros(len(trees) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+
+    def cat(field, dtype, width=None):
+        parts = []
+        for t in trees:
+            a = getattr(t, field)
+            if width is not None:
+                b = np.zeros((a.shape[0], width), dtype=dtype)
+                b[:, :a.shape[1]] = a
+                a = b
+            parts.append(np.ascontiguousarray(a, dtype=dtype).reshape(-1))
+        return np.concatenate(parts) if parts else np.zeros(1, dtype=dtype)
+
+    host = {"tree_off": off, "left": cat("left", np.int32), "right": cat("right", np.int32),
+            "leaf_class": cat("leaf_class", np.int32), "proj_nnz": cat("proj_nnz", np.int32),
+            "feat": cat("feat", np.int32, cap), "sign": cat("sign", np.int8, cap),
+            "threshold": cat("threshold", np.float32)}
+    dev = {k: torch.from_numpy(v).to(device) for k, v in host.items()}
+    return DeviceForest(len(trees), n_classes, cap, dev)
+
+
+def so_predict(X, forest: DeviceForest, want_votes: bool = False, stream=None):
+    """Majority-vote prediction of every column of X (cuda float32 [d, n]).
+    Returns (pred int32 [n], votes int32 [n, C] or None) as cuda tensors."""
+    import torch
+    assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    n, d = X.shape[1], X.shape[0]
+    pred = torch.empty(n, dtype=torch.int32, device=X.device)
+    votes = torch.empty((n, forest.n_classes), dtype=torch.int32, device=X.device) if want_votes else None
+    f = forest.c()
+    _check(lib().so_predict(X.data_ptr(), n, d, X.stride(0), C.byref(f), votes.data_ptr() if votes is not None else None,
+                            pred.data_ptr(), _stream(stream)))
+    return pred, votes
 
 
 def so_autotune(ds: DeviceDataset, n_proj: int, lam: float, cap: int, params: so_split_params, stream=None):

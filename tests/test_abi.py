@@ -118,3 +118,17 @@ def test_autotune_argument_checks(L):
     for args in ((0, 1.5, 8), (8, -1.0, 8), (8, 1.5, 0), (8, 1.5, 33)):
         assert L.so_autotune(C.byref(ds), args[0], args[1], args[2], C.byref(p), None, None, C.byref(k),
                              None) == S.SO_EINVAL
+
+
+def test_predict_argument_checks(L):
+    from paper_2603_00326_b300 import soforest as S
+    f = S.so_forest(1, 2, 8, None, None, None, None, None, None, None, None)
+    pred = C.c_int32(0)
+    # NULL forest arrays, bad class count, NULL pred: rejected before any launch
+    assert L.so_predict(None, 0, 4, 0, C.byref(f), None, C.byref(pred), None) == S.SO_EINVAL
+    f2 = S.so_forest(0, 9, 8, None, None, None, None, None, None, None, None)
+    assert L.so_predict(None, 0, 4, 0, C.byref(f2), None, C.byref(pred), None) == S.SO_EINVAL
+    f3 = S.so_forest(0, 2, 8, None, None, None, None, None, None, None, None)
+    assert L.so_predict(None, 0, 4, 0, C.byref(f3), None, None, None) == S.SO_EINVAL
+    # an empty forest over zero samples is a no-op
+    assert L.so_predict(None, 0, 4, 0, C.byref(f3), None, C.byref(pred), None) == S.SO_OK

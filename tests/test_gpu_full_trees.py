@@ -2,7 +2,8 @@
 the oracle (tests/tree_check.py): every node's samples, counts and children by
 routing the root samples with the oracle's projection arithmetic, and a
 spread of nodes (root, each depth band, random internal nodes, searched
-leaves) re-searched by the oracle from its own projection sampler.
+leaves) re-searched by the oracle from its own projection sampler; then the
+tree's predictions for 50,000 rows against the oracle's traversal.
 
 * forest_2m: n=2M, d=256 lognormal features, 8-sparse median-centred labels
   with 10% flips, bootstrap root, 128 projections/node, T=1024 -- tree 0 of
@@ -14,6 +15,7 @@ leaves) re-searched by the oracle from its own projection sampler.
 import numpy as np
 import pytest
 
+from oracle import so_oracle as O
 from paper_2603_00326_b300 import datagen as G
 from tests import gpu_util as U
 from tests.tree_check import choose_nodes, route_and_sample
@@ -32,7 +34,11 @@ def _grow_and_check(S, ds_np, root, p, seed, tree_id, n_internal):
     ds = U.upload_dataset(ds_np.X, ds_np.y, ds_np.n_classes)
     tp = S.tree_params(p["n_proj"], p["lam"], p["cap"], p["n_bins"], p["sort_below"], False, seed, tree_id, -1)
     gt = S.so_train_tree(ds, U.i32(root), tp)
-    del ds
+    # inference with the full-size tree on a sample of rows
+    rows = np.sort(np.random.default_rng(tree_id + 7).choice(ds_np.n, size=50000, replace=False)).astype(np.int32)
+    pred, _ = S.so_predict(ds.X, S.upload_forest([gt], ds_np.n_classes))
+    np.testing.assert_array_equal(pred.cpu().numpy()[rows], O.predict_tree_c(gt, ds_np.X, rows))
+    del ds, pred
     U.torch_cuda().cuda.empty_cache()
     ids = choose_nodes(gt, n_internal=n_internal, n_leaves=6, seed=tree_id + 1)
     n = route_and_sample(gt, ds_np.X, ds_np.y, ds_np.n_classes, root, n_proj=p["n_proj"], lam=p["lam"],
