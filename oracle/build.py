@@ -21,7 +21,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".tmp"
-    cmd = ["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"]
+    cmd = ["gcc", *CFLAGS, SRC, "-o", tmp, "-lm", "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

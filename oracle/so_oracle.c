@@ -50,6 +50,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -604,4 +605,78 @@ void orc_predict_tree(const orc_tree *t, const float *X, int64_t ld, const int32
         }
         cls_out[i] = t->leaf_class[id];
     }
+}
+
+
+/*
+ * The same split search with the projections divided into contiguous ranges,
+ * one per thread (each range searched by orc_split_search above), and the
+ * range results taken in projection order with the same strict comparison,
+ * so the result is the single-threaded one.  Used to time the oracle on all
+ * host cores; debug outputs are not offered.  Returns 0 or -1.
+ */
+typedef struct {
+    const float *X; int64_t ld; const uint8_t *y; int C; const int32_t *idx; int64_t n;
+    int p0, p1; const int32_t *ptr; const int32_t *feat; const int8_t *sign;
+    int B, sort_below, hist_only;
+    orc_split res; int64_t lc[ORC_MAX_CLASSES]; int rc;
+} orc_range_job;
+
+static void *orc_range_run(void *arg)
+{
+    orc_range_job *j = (orc_range_job *)arg;
+    j->rc = orc_split_search(j->X, j->ld, j->y, j->C, j->idx, j->n, j->p1 - j->p0, j->ptr + j->p0,
+                             j->feat, j->sign, j->B, j->sort_below, j->hist_only, &j->res, j->lc,
+                             NULL, NULL, NULL);
+    return NULL;
+}
+
+int orc_split_search_mt(const float *X, int64_t ld, const uint8_t *y, int C,
+                        const int32_t *idx, int64_t n, int P, const int32_t *ptr,
+                        const int32_t *feat, const int8_t *sign, int B, int sort_below,
+                        int hist_only, int n_threads, orc_split *out, int64_t *left_counts)
+{
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > P) n_threads = P > 0 ? P : 1;
+    orc_range_job *jobs = (orc_range_job *)calloc((size_t)n_threads, sizeof(orc_range_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -1; }
+    for (int t = 0; t < n_threads; t++) {
+        orc_range_job *j = &jobs[t];
+        j->X = X; j->ld = ld; j->y = y; j->C = C; j->idx = idx; j->n = n;
+        j->p0 = (int)((int64_t)P * t / n_threads);
+        j->p1 = (int)((int64_t)P * (t + 1) / n_threads);
+        j->ptr = ptr; j->feat = feat; j->sign = sign;
+        j->B = B; j->sort_below = sort_below; j->hist_only = hist_only;
+    }
+    int started = 0;
+    for (int t = 1; t < n_threads; t++) {
+        if (pthread_create(&th[t], NULL, orc_range_run, &jobs[t]) != 0) break;
+        started = t;
+    }
+    orc_range_run(&jobs[0]);
+    for (int t = started + 1; t < n_threads; t++) orc_range_run(&jobs[t]);  /* threads that failed to start */
+    for (int t = 1; t <= started; t++) pthread_join(th[t], NULL);
+    int rc = 0;
+    memset(out, 0, sizeof(*out));
+    out->proj = -1;
+    out->cand = -1;
+    int64_t bestL[ORC_MAX_CLASSES] = {0};
+    double best = 0.0;
+    for (int t = 0; t < n_threads; t++) {
+        orc_range_job *j = &jobs[t];
+        if (j->rc) rc = -1;
+        out->path = j->res.path;
+        if (j->res.valid && j->res.gain > best) {
+            best = j->res.gain;
+            *out = j->res;
+            out->proj = j->res.proj + j->p0;
+            memcpy(bestL, j->lc, sizeof(bestL));
+        }
+    }
+    if (left_counts)
+        for (int c = 0; c < C; c++)
+            left_counts[c] = bestL[c];
+    free(jobs); free(th);
+    return rc;
 }

@@ -63,6 +63,10 @@ def lib():
                                      C.c_void_p]
         L.orc_tree_free.restype = None
         L.orc_tree_free.argtypes = [C.c_void_p]
+        L.orc_split_search_mt.restype = C.c_int
+        L.orc_split_search_mt.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
+                                          C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.orc_predict_tree.restype = None
         L.orc_predict_tree.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                        C.c_int64, C.c_void_p]
@@ -218,6 +222,29 @@ def split_search(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
         raise ValueError("orc_split_search failed")
     return SplitResult(out.valid, out.proj, out.path, out.cand, np.float32(out.threshold),
                        out.gain, out.n_left, out.n_right, lc, mm, hist, gains)
+
+
+def split_search_mt(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
+                    ptr: np.ndarray, feat: np.ndarray, sign: np.ndarray, n_bins: int = 256,
+                    sort_below: int = 1024, hist_only: bool = False, n_threads: int = 1) -> SplitResult:
+    """split_search with the projections divided over n_threads host threads
+    (same result; no debug outputs)."""
+    X = _c(X, np.float32)
+    y = _c(y, np.uint8)
+    idx = _c(idx, np.int32)
+    ptr = _c(ptr, np.int32)
+    feat = _c(feat, np.int32)
+    sign = _c(sign, np.int8)
+    P = ptr.shape[0] - 1
+    out = OrcSplit()
+    lc = np.zeros(n_classes, dtype=np.int64)
+    rc = lib().orc_split_search_mt(_p(X), X.shape[1], _p(y), n_classes, _p(idx), idx.shape[0], P, _p(ptr),
+                                   _p(feat), _p(sign), n_bins, sort_below, int(bool(hist_only)), n_threads,
+                                   C.byref(out), _p(lc))
+    if rc:
+        raise ValueError("orc_split_search_mt failed")
+    return SplitResult(out.valid, out.proj, out.path, out.cand, np.float32(out.threshold),
+                       out.gain, out.n_left, out.n_right, lc)
 
 
 def partition(X: np.ndarray, idx: np.ndarray, feat, sign, threshold: float):

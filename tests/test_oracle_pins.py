@@ -506,3 +506,23 @@ def test_hist_and_sort_agree_on_aligned_data():
     rs = O.split_search(X, y, 2, idx, ptr, f, s, sort_below=100)
     rh = O.split_search(X, y, 2, idx, ptr, f, s, n_bins=8, hist_only=True)
     assert rs.n_left == rh.n_left and rs.gain == rh.gain
+
+
+def test_threaded_split_search_equals_plain():
+    """The host-threaded oracle (used to time the CPU baseline on all cores)
+    returns the plain split search's result for every thread count."""
+    import oracle as O2
+    from paper_2603_00326_b300 import datagen as G2
+    ds = G2.tree_small(n=3000, d=12, seed=15)
+    rng = np.random.default_rng(2)
+    pr = G2.random_projections(rng, 29, 12, 1.5, 8)
+    idx = G2.all_indices(ds.n)
+    for T, ho in ((1024, True), (4000, False)):
+        a = O2.split_search(ds.X, ds.y, 2, idx, pr.ptr, pr.feat, pr.sign, sort_below=T, hist_only=ho)
+        for nt in (1, 2, 5, 29, 64):
+            b = O2.split_search_mt(ds.X, ds.y, 2, idx, pr.ptr, pr.feat, pr.sign, sort_below=T, hist_only=ho,
+                                   n_threads=nt)
+            assert (a.valid, a.proj, a.cand, a.path, a.n_left) == (b.valid, b.proj, b.cand, b.path, b.n_left)
+            assert np.float32(a.threshold).tobytes() == np.float32(b.threshold).tobytes()
+            assert np.float64(a.gain).tobytes() == np.float64(b.gain).tobytes()
+            np.testing.assert_array_equal(a.left_counts, b.left_counts)
