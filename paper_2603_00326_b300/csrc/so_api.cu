@@ -646,49 +646,107 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
     Frontier cur = fa, nxt = fb;
     int32_t *cidx = idx_a, *nidx = idx_b;
     const float eps = effective_eps(tp->rescore_rel_eps, C);
-    while (m > 0) {
-      for (int64_t j0 = 0; j0 < m; j0 += Mb) {
-        const int32_t mb = (int32_t)std::min<int64_t>(Mb, m - j0);
-        SO_CK(launch_sample(mb, cur.key + j0, P, ds->d, tp->lambda, cap, snnz, sfeat, ssign, sbeg, send, cs));
-        SearchArgs a;
-        a.ds = dv;
-        a.idx = cidx;
-        a.n_total = n_level;
-        a.node_off = cur.off + j0;
-        a.m = mb;
-        a.pv = ProjView{sbeg, send, sfeat, ssign, P};
-        a.B = B;
-        a.T = T;
-        a.hist_only = HO;
-        a.eps = eps;
-        a.max_nnz = cap;
-        a.out = spl + j0;
-        a.left_counts = lc + j0 * C;
-        a.vbuf = vbuf;
-        SO_CK(launch_search(a, ss, cs));
-        SO_CK(launch_tree_record_splits((int32_t)j0, mb, cur, spl, snnz, sfeat, ssign, P, cap, td, cs));
+    // Each level's launches (sampling, split search, split records, next
+    // frontier, partition, statistics copy) are captured into a CUDA graph on
+    // a private stream and launched as one; the executable graph is updated
+    // in place from level to level while the launch sequence keeps its shape.
+    // With tracing on, the launches go to the stream directly.
+    LevelStats* hsp = nullptr;
+    SO_CK(cudaMallocHost(&hsp, sizeof(LevelStats)));  // graph memcpy nodes need page-locked memory
+    struct LevelResources {
+      LevelStats* pinned = nullptr;
+      cudaStream_t stream = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      ~LevelResources() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (stream) cudaStreamDestroy(stream);
+        if (pinned) cudaFreeHost(pinned);
       }
-      SO_CK(launch_tree_level((int32_t)m, cur, nxt, spl, lc, tp->max_depth, n_nodes, td, pn, tiles, total, stats,
-                              cs));
-      PartArgs pa;
-      pa.ds = dv;
-      pa.idx_in = cidx;
-      pa.idx_out = nidx;
-      pa.n = n_level;
-      pa.node_off = cur.off;
-      pa.m = (int32_t)m;
-      pa.nodes = pn;
-      pa.feat = td.feat;
-      pa.sign = td.sign;
-      pa.flags = flags;
-      pa.tile_cnt = ptiles;
-      pa.ones_total = ones;
-      pa.err = &stats->err;
-      pa.n_out = n_root;
-      pa.fix_node = nullptr;
-      SO_CK(launch_partition(pa, cs));
-      SO_CK(cudaMemcpyAsync(&hs, stats, sizeof(LevelStats), cudaMemcpyDeviceToHost, cs));
-      SO_CK(cudaStreamSynchronize(cs));
+    } lr;
+    lr.pinned = hsp;
+    bool use_graph = !profiling_on();
+    if (use_graph && cudaStreamCreateWithFlags(&lr.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      lr.stream = nullptr;
+      use_graph = false;
+    }
+    const cudaStream_t ls = use_graph ? lr.stream : cs;
+    while (m > 0) {
+      auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int64_t j0 = 0; j0 < m && e == cudaSuccess; j0 += Mb) {
+          const int32_t mb = (int32_t)std::min<int64_t>(Mb, m - j0);
+          e = launch_sample(mb, cur.key + j0, P, ds->d, tp->lambda, cap, snnz, sfeat, ssign, sbeg, send, ls);
+          if (e != cudaSuccess) break;
+          SearchArgs a;
+          a.ds = dv;
+          a.idx = cidx;
+          a.n_total = n_level;
+          a.node_off = cur.off + j0;
+          a.m = mb;
+          a.pv = ProjView{sbeg, send, sfeat, ssign, P};
+          a.B = B;
+          a.T = T;
+          a.hist_only = HO;
+          a.eps = eps;
+          a.max_nnz = cap;
+          a.out = spl + j0;
+          a.left_counts = lc + j0 * C;
+          a.vbuf = vbuf;
+          e = launch_search(a, ss, ls);
+          if (e == cudaSuccess)
+            e = launch_tree_record_splits((int32_t)j0, mb, cur, spl, snnz, sfeat, ssign, P, cap, td, ls);
+        }
+        if (e == cudaSuccess)
+          e = launch_tree_level((int32_t)m, cur, nxt, spl, lc, tp->max_depth, n_nodes, td, pn, tiles, total, stats,
+                                ls);
+        if (e != cudaSuccess) return e;
+        PartArgs pa;
+        pa.ds = dv;
+        pa.idx_in = cidx;
+        pa.idx_out = nidx;
+        pa.n = n_level;
+        pa.node_off = cur.off;
+        pa.m = (int32_t)m;
+        pa.nodes = pn;
+        pa.feat = td.feat;
+        pa.sign = td.sign;
+        pa.flags = flags;
+        pa.tile_cnt = ptiles;
+        pa.ones_total = ones;
+        pa.err = &stats->err;
+        pa.n_out = n_root;
+        pa.fix_node = nullptr;
+        e = launch_partition(pa, ls);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hsp, stats, sizeof(LevelStats), cudaMemcpyDeviceToHost, ls);
+        return e;
+      };
+      cudaError_t e;
+      if (use_graph) {
+        e = cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          const cudaError_t e1 = enqueue();
+          cudaGraph_t g = nullptr;
+          const cudaError_t e2 = cudaStreamEndCapture(ls, &g);
+          e = e1 != cudaSuccess ? e1 : e2;
+          if (e == cudaSuccess && lr.exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(lr.exec, g, &info) != cudaSuccess) {
+              (void)cudaGetLastError();
+              cudaGraphExecDestroy(lr.exec);
+              lr.exec = nullptr;
+            }
+          }
+          if (e == cudaSuccess && !lr.exec) e = cudaGraphInstantiate(&lr.exec, g, 0);
+          if (e == cudaSuccess) e = cudaGraphLaunch(lr.exec, ls);
+          if (g) cudaGraphDestroy(g);
+        }
+      } else {
+        e = enqueue();
+      }
+      SO_CK(e);
+      SO_CK(cudaStreamSynchronize(ls));
+      hs = *hsp;
       if (hs.err) return fail(SO_EINTERNAL, "partition consistency check failed (code %d)", hs.err);
       n_nodes += hs.new_nodes;
       if (n_nodes > Ncap) return fail(SO_EINTERNAL, "node capacity exceeded");

@@ -126,6 +126,9 @@ struct SearchScratch {
 void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int32_t P, int32_t C,
                   int32_t B, int32_t T, int32_t hist_only);
 
+// Whether per-stage tracing is on (so_profile_enable).
+bool profiling_on();
+
 // Records a CUDA event pair around a launch group when profiling is on, and
 // counts its kernel launches.
 class ProfScope {

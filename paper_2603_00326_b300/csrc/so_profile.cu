@@ -47,6 +47,8 @@ int stage_id(const char* name) {
 }
 }  // namespace
 
+bool profiling_on() { return g_on.load(std::memory_order_relaxed) != 0; }
+
 ProfScope::ProfScope(const char* name, cudaStream_t st, int launches) : st_(st) {
   g_launches.fetch_add(launches, std::memory_order_relaxed);
   if (!g_on.load(std::memory_order_relaxed)) return;
