@@ -425,7 +425,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (histogram fill)
     # DRAM bytes (read + write) of one k_hist_staged launch on this workload, from the ncu capture
     # summarised in profiles/k_hist_staged_root_4m.md; set to None whenever that kernel changes.
-    K_HIST_TRAFFIC_BYTES = 1_099_836_000 + 7_728_384
+    K_HIST_TRAFFIC_BYTES = 1_099_905_000 + 7_710_208
     hbm, peak_kind = peaks()
     used_feats = np.unique(pr.feat).size
     alg_bytes = used_feats * n * 4 + n * 4 + n * 1  # feature columns + index list + labels, one pass

@@ -718,34 +718,100 @@ struct BinParams {
   int fast;
 };
 
+// Packed form of project_tile: sample pairs in FP32x2 registers (fma(+-1, x,
+// acc) per lane of the pair, the same single rounding).
 template <int V, int NQ>
-__device__ __forceinline__ void hist_tile_fast(unsigned tile, unsigned lab, unsigned dpk, int k, int lane,
-                                               const BinParams& bp, unsigned C4, unsigned limit) {
-  float acc[V * NQ];
-  int yo[V * NQ];
-  project_tile<V, NQ>(tile, dpk, k, lane, acc);
-  tile_labels<V, NQ>(lab, lane, yo);
+__device__ __forceinline__ void project_tile2(unsigned tile, unsigned dpk, int k, int lane,
+                                              float2 (&acc)[V * NQ / 2]) {
+  const unsigned base = tile + 4u * V * lane;
 #pragma unroll
-  for (int i = 0; i < V * NQ; ++i) {
-    // q = round(v / W + c') by the 1.5 * 2^23 shift; then the exact boundary
-    // t_{q+1} = min + (q+1) * W with two roundings decides between q and q+1
-    const float tq = __fadd_rn(__fmaf_rn(acc[i], bp.inv_w, bp.c), kMagic);
-    const float q1 = __fadd_rn(tq, 1.0f - kMagic);
-    const float tb = __fadd_rn(bp.mn, __fmul_rn(q1, bp.W));
-    unsigned a = __float_as_uint(tq) * C4 + (bp.hb + (unsigned)yo[i]);
-    if (tb <= acc[i]) a += C4;
-    reds_add(min(a, limit), bp.inc);
+  for (int i = 0; i < V * NQ / 2; ++i) acc[i] = make_float2(0.0f, 0.0f);
+  auto term = [&](uint32_t w) {
+    const float s = desc_sign(w);
+    const float2 s2 = make_float2(s, s);
+    const unsigned row = base + (w & 0xffffu);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (V == 4) {
+        const float4 x = lds_f4(row + 512 * q);
+        acc[2 * q] = ffma2(s2, make_float2(x.x, x.y), acc[2 * q]);
+        acc[2 * q + 1] = ffma2(s2, make_float2(x.z, x.w), acc[2 * q + 1]);
+      } else {
+        acc[q] = ffma2(s2, lds_f2(row + 256 * q), acc[q]);
+      }
+    }
+  };
+  for (int j0 = 0; j0 < k; j0 += 4) {
+    const uint4 w = lds_u4(dpk + 4u * j0);
+    term(w.x);
+    if (j0 + 1 >= k) break;
+    term(w.y);
+    if (j0 + 2 >= k) break;
+    term(w.z);
+    if (j0 + 3 >= k) break;
+    term(w.w);
+  }
+}
+
+// Label offsets of the tile (one int per sample, decoded once per tile), in
+// project_tile's order.
+template <int V, int NQ>
+__device__ __forceinline__ void tile_offsets(unsigned yo_tile, int lane, int (&yo)[V * NQ]) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (V == 4) {
+      const uint4 y = lds_u4(yo_tile + 4u * (128 * q + 4 * lane));
+      yo[4 * q] = (int)y.x;
+      yo[4 * q + 1] = (int)y.y;
+      yo[4 * q + 2] = (int)y.z;
+      yo[4 * q + 3] = (int)y.w;
+    } else {
+      const float2 y = lds_f2(yo_tile + 4u * (64 * q + 2 * lane));
+      yo[2 * q] = __float_as_int(y.x);
+      yo[2 * q + 1] = __float_as_int(y.y);
+    }
+  }
+}
+
+template <int V, int NQ>
+__device__ __forceinline__ void hist_tile_fast(unsigned tile, unsigned yo_tile, unsigned dpk, int k, int lane,
+                                               const BinParams& bp, unsigned C4, unsigned limit) {
+  float2 acc[V * NQ / 2];
+  int yo[V * NQ];
+  project_tile2<V, NQ>(tile, dpk, k, lane, acc);
+  tile_offsets<V, NQ>(yo_tile, lane, yo);
+  const float2 inv2 = make_float2(bp.inv_w, bp.inv_w);
+  const float2 c2 = make_float2(bp.c, bp.c);
+  const float2 m2 = make_float2(kMagic, kMagic);
+  const float2 m1 = make_float2(1.0f - kMagic, 1.0f - kMagic);
+#pragma unroll
+  for (int i = 0; i < V * NQ / 2; ++i) {
+    // q = round(v / W + c') by the 1.5 * 2^23 shift (packed: one fused
+    // multiply-add, then additions that cannot fuse with it); the exact
+    // boundary t_{q+1} = min + (q+1) * W with two roundings (scalar, so the
+    // multiply and the add stay separate) decides between q and q+1
+    const float2 e = ffma2(acc[i], inv2, c2);
+    const float2 tq = fadd2(e, m2);
+    const float2 q1 = fadd2(tq, m1);
+    const float tbx = __fadd_rn(bp.mn, __fmul_rn(q1.x, bp.W));
+    const float tby = __fadd_rn(bp.mn, __fmul_rn(q1.y, bp.W));
+    unsigned ax = __float_as_uint(tq.x) * C4 + (bp.hb + (unsigned)yo[2 * i]);
+    unsigned ay = __float_as_uint(tq.y) * C4 + (bp.hb + (unsigned)yo[2 * i + 1]);
+    if (tbx <= acc[i].x) ax += C4;
+    if (tby <= acc[i].y) ay += C4;
+    reds_add(min(ax, limit), bp.inc);
+    reds_add(min(ay, limit), bp.inc);
   }
 }
 
 // exact estimate-and-correct rule for projections outside the fast condition
 template <int V, int NQ>
-__device__ __forceinline__ void hist_tile_slow(unsigned tile, unsigned lab, unsigned dpk, int k, int lane,
+__device__ __forceinline__ void hist_tile_slow(unsigned tile, unsigned yo_tile, unsigned dpk, int k, int lane,
                                                const BinParams& bp, int B, int C, int wbase, uint32_t* s_hist) {
   float acc[V * NQ];
   int yo[V * NQ];
   project_tile<V, NQ>(tile, dpk, k, lane, acc);
-  tile_labels<V, NQ>(lab, lane, yo);
+  tile_offsets<V, NQ>(yo_tile, lane, yo);
 #pragma unroll
   for (int i = 0; i < V * NQ; ++i)
     if (yo[i] >= 0) atomicAdd(&s_hist[wbase + bin_of(acc[i], bp.mn, bp.W, bp.inv_w, B) * C + (yo[i] >> 2)], bp.inc);
@@ -757,7 +823,8 @@ __device__ __forceinline__ void hist_tile_slow(unsigned tile, unsigned lab, unsi
 // parameters in registers.
 template <int V, int NQ>
 __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
-                                          int U, bool contig, float* s_tile, const uint8_t* s_lab, const int* s_rowfeat,
+                                          int U, bool contig, float* s_tile, const uint8_t* s_lab, int* s_yo,
+                                          const int* s_rowfeat,
                                           const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk, const uint32_t* s_dpk,
                                           int kmax, const float4* s_bpf, const int4* s_bpi, int B, int HS,
                                           unsigned C4, unsigned limit, uint32_t* s_hist, int lane, int warp) {
@@ -780,18 +847,31 @@ __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* 
   }
   const unsigned limit_abs = su32(s_hist) + limit;
   const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig);
-  if (ntile > 0) stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
+  // label byte offsets of tile t into s_yo[t % 3], written with tile t's copies
+  auto tile_yo = [&](int t, int b) {
+    if ((int)threadIdx.x < St) s_yo[b * 256 + threadIdx.x] = label_off8(s_lab[t * St + threadIdx.x]);
+  };
+  if (ntile > 0) {
+    stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
+    tile_yo(0, 0);
+  }
   cp_async_commit();
-  if (ntile > 1) stager_issue(sg, ds, idx, it, 1, St, U, s_rowoff, s_tile + kTileF);
+  if (ntile > 1) {
+    stager_issue(sg, ds, idx, it, 1, St, U, s_rowoff, s_tile + kTileF);
+    tile_yo(1, 1);
+  }
   cp_async_commit();
   int bc = 0, bn = 1, bi = 2;  // buffers of tiles tt, tt + 1, tt + 2
   for (int tt = 0; tt < ntile; ++tt) {
     cp_async_wait1();
     __syncthreads();  // tile tt visible; every warp done with tile tt-1
-    if (tt + 2 < ntile) stager_issue(sg, ds, idx, it, tt + 2, St, U, s_rowoff, s_tile + bi * kTileF);
+    if (tt + 2 < ntile) {
+      stager_issue(sg, ds, idx, it, tt + 2, St, U, s_rowoff, s_tile + bi * kTileF);
+      tile_yo(tt + 2, bi);
+    }
     cp_async_commit();
     const unsigned tile = su32(s_tile) + 4u * kTileF * bc;
-    const unsigned lab = su32(s_lab) + (unsigned)(tt * St);
+    const unsigned lab = su32(s_yo) + 4u * 256 * bc;
     bc = bn;
     bn = bi;
     bi = bi == 2 ? 0 : bi + 1;
@@ -874,7 +954,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   // every region starts on a 16-byte boundary
   float* s_tile = reinterpret_cast<float*>(s_raw);                           // [3][kTileF]
   uint8_t* s_lab = reinterpret_cast<uint8_t*>(s_tile + 3 * kTileF);          // [kMaxItem + 512] item labels
-  uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_lab + kMaxItem + 512);    // [hist_words]
+  int* s_yo = reinterpret_cast<int*>(s_lab + kMaxItem + 512);                // [3][256] tile label offsets
+  uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_yo + 3 * 256);            // [hist_words]
   uint32_t* s_dpk = s_hist + hist_words;                                     // [kHistPGMax*KMAX]
   int* s_dk = reinterpret_cast<int*>(s_dpk + kHistPGMax * KMAX);             // [kHistPGMax]
   int* s_assign = s_dk + kHistPGMax;                                         // [kHistPGMax]
@@ -944,13 +1025,13 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         hist_item_buf(vbuf, n_total, it, su32(s_lab), s_assign, nslot, s_bpf, s_bpi, B, C, HS, C4,
                       su32(s_hist) + limit, s_hist, lane, warp);
       } else if (St == 256)
-        hist_item<4, 2>(ds, idx, it, U, contig, s_tile, s_lab, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
+        hist_item<4, 2>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
                      s_bpi, B, HS, C4, limit, s_hist, lane, warp);
       else if (St == 128)
-        hist_item<4, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
+        hist_item<4, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
                      s_bpi, B, HS, C4, limit, s_hist, lane, warp);
       else
-        hist_item<2, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
+        hist_item<2, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
                      s_bpi, B, HS, C4, limit, s_hist, lane, warp);
     } else {
       // direct path for wide groups (rare): one warp per projection, gathers
@@ -1009,7 +1090,7 @@ size_t mm_smem_bytes(int /*d*/, int kmax) {
 size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG) {
   const int npair = (PG + 1) >> 1;
   const size_t hist_words = ((size_t)npair * (B + 1) * C + 1 + 3) & ~(size_t)3;
-  return (size_t)3 * kTileF * 4 + kMaxItem + 512 + hist_words * 4 + (size_t)kHistPGMax * kmax * 4 +
+  return (size_t)3 * kTileF * 4 + kMaxItem + 512 + 3 * 256 * 4 + hist_words * 4 + (size_t)kHistPGMax * kmax * 4 +
          kHistPGMax * 8 + kStUMax * 12;
 }
 
