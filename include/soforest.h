@@ -137,7 +137,10 @@ so_status so_split_search(const so_dataset *ds, const int32_t *idx, int64_t n_no
  *                  node_off[m] <= n_total (the length of idx).
  *  out_dev         device so_split [m].
  *  left_counts_dev device int64 [m*n_classes] or NULL.
- *  workspace       as above, sized by so_split_search_ws_bytes(m, n_total, ...). */
+ *  workspace       as above, sized by so_split_search_ws_bytes(m, n_total, ...);
+ *                  for m > 1 it includes a [n_proj][n_total] float buffer in
+ *                  which the min/max pass keeps the histogram-path samples'
+ *                  projected values for the histogram pass. */
 so_status so_split_search_batch(const so_dataset *ds, const int32_t *idx, int64_t n_total,
                                 const int64_t *node_off, int32_t m, const so_projs *projs,
                                 const so_split_params *params, so_split *out_dev,

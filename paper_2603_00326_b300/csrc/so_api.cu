@@ -176,6 +176,19 @@ size_t search_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B,
   return cv.used + 256;
 }
 
+// A batch of more than one node also reserves a [P][n_total] float buffer:
+// its histogram-path nodes are gathered, so the min/max pass keeps their
+// projected values for the histogram pass (4 bytes per sample-projection
+// instead of a second gather of the feature columns).
+size_t batch_vbuf_floats(int32_t m, int64_t n_total, int32_t P) {
+  return m > 1 ? (size_t)P * (size_t)n_total : 0;
+}
+
+size_t batch_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, int32_t T, int32_t hist_only) {
+  const size_t vb = batch_vbuf_floats(m, n_total, P);
+  return search_bytes(m, n_total, P, C, B, T, hist_only) + (vb ? vb * sizeof(float) + 256 : 0);
+}
+
 template <typename F>
 so_status guarded(F f) {
   try {
@@ -225,7 +238,7 @@ size_t so_split_search_ws_bytes(int32_t m, int64_t n_total, int32_t n_proj, int3
                                 const so_split_params* params) {
   if (!params || m < 0 || n_proj < 1 || n_classes < 1) return 0;
   const size_t extra = 4096 + sizeof(so_split) + 64 * (size_t)n_classes;
-  return search_bytes(m, n_total, n_proj, n_classes, params->n_bins, params->sort_below, params->hist_only) + extra;
+  return batch_bytes(m, n_total, n_proj, n_classes, params->n_bins, params->sort_below, params->hist_only) + extra;
 }
 
 so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_t n_total, const int64_t* node_off,
@@ -240,7 +253,7 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     if (n_total < 0 || n_total > INT32_MAX) return fail(SO_EINVAL, "n_total out of range");
     cudaStream_t cs = (cudaStream_t)stream;
     const int C = ds->n_classes, P = projs->n_proj;
-    const size_t need = search_bytes(m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only);
+    const size_t need = batch_bytes(m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only);
     ArenaLease lease;
     char* base = (char*)workspace;
     size_t cap = ws_bytes;
@@ -256,8 +269,11 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     cv.cap = cap;
     SearchScratch s;
     carve_search(cv, s, m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only);
+    const size_t vbf = batch_vbuf_floats(m, n_total, P);
+    float* vbuf = vbf ? cv.take<float>(vbf) : nullptr;
     if (!cv.ok()) return fail(SO_ENOMEM, "workspace too small");
     SearchArgs a;
+    a.vbuf = vbuf;
     a.ds = view_of(ds);
     a.idx = idx;
     a.n_total = n_total;
