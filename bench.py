@@ -227,7 +227,7 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1):
         from paper_2603_00326_b300 import forest as F
         fs = G.forest_2m()
         fp = G.WORKLOAD_PARAMS["forest_2m"]
-        dd = S.DeviceDataset(torch.from_numpy(fs.X).to(dev), torch.from_numpy(fs.y).to(dev), 2)
+        dd = S.DeviceDataset(torch.from_numpy(fs.X).to(dev), torch.from_numpy(fs.y).to(dev), 2).with_row_major()
         cfg = F.ForestConfig(n_trees=forest_trees, n_proj=fp["n_proj"], lam=fp["lam"], cap=fp["cap"],
                              sort_below=fp["sort_below"])
         F.train_forest(F.ForestConfig(n_trees=1, n_proj=8, lam=1.5, cap=8), dd)  # warm-up

@@ -53,7 +53,11 @@ typedef enum {
 
 /* Training data, device resident (the paper preloads the whole table once,
  * Section 3.3).  X: device, column-major, X[f*ld + i], f < d, i < n.
- * y: device, n labels in [0, n_classes). */
+ * y: device, n labels in [0, n_classes).
+ * Xr: optional device row-major copy of the same values, Xr[i*d + f], or
+ * NULL.  When given, the min/max pass reads the feature rows of scattered
+ * samples from it (one sample's features share DRAM sectors) instead of
+ * gathering one sector per (sample, feature) from X; results do not change. */
 typedef struct {
     const float *X;
     int64_t n;          /* samples, 1 .. 2^31-1 */
@@ -61,6 +65,7 @@ typedef struct {
     int64_t ld;         /* leading dimension, >= n */
     const uint8_t *y;
     int32_t n_classes;  /* 1..8 */
+    const float *Xr;    /* optional row-major copy [n][d], or NULL */
 } so_dataset;
 
 /* Sparse projections in CSR form (Section 3: "a sparse list" of non-zero
@@ -116,6 +121,11 @@ typedef struct {
     int64_t n_left;
     int64_t n_right;
 } so_split;
+
+/* Fills the optional row-major copy of a feature matrix (so_dataset.Xr):
+ * Xr[i*d + f] = X[f*ld + i] for i < n, f < d.  X, Xr: device; Xr holds n*d
+ * floats and is owned by the caller.  Asynchronous on `stream`. */
+so_status so_row_major(const float *X, int64_t n, int32_t d, int64_t ld, float *Xr, void *stream);
 
 /* Best split of ONE node (the paper's node-at-a-time GPU call, Section 3.3).
  *  idx        device, n_node sample indices (repeats allowed, e.g. bootstrap).

@@ -151,6 +151,7 @@ DatasetView view_of(const so_dataset* ds) {
   v.y = ds->y;
   v.d = ds->d;
   v.C = ds->n_classes;
+  v.Xr = ds->Xr;
   return v;
 }
 

@@ -34,7 +34,7 @@ constexpr int kStThreads = 1024;         // threads of the staged kernels (32 wa
 constexpr int kStWarps = kStThreads / 32;
 constexpr int kTileF = 8192;             // floats per tile buffer (32 KB); two buffers
 constexpr int kStUMax = kTileF / 64;     // rows of a tile at St = 64 -> 128
-constexpr int kMmUMax = kStUMax;
+constexpr int kMmUMax = kTileF / 68;     // 120: every min/max group also fits the padded row-major tile
 constexpr int kStMaxWords = 2048;        // feature bitmap words (d <= 65536)
 constexpr int kMmPPW = 8;                // min/max: projections per warp
 constexpr int kMmGroup = kStWarps * kMmPPW;  // 256 projections per min/max group
@@ -283,16 +283,30 @@ struct Stager {
   int dst0, dst1;
   int col;
   bool vec;
+  // row-major gather form: the thread copies row r of every 1024/Ur-th
+  // sample column from the row-major copy (feature frow, -1: no row)
+  bool rowmaj;
+  int Ur, r, frow, Sp;
 };
 
 __device__ __forceinline__ Stager stager_init(const DatasetView& ds, const int32_t* __restrict__ idx,
-                                              const ItemPos& it, int St, int U, const int* s_rowfeat, bool contig) {
+                                              const ItemPos& it, int St, int U, const int* s_rowfeat, bool contig,
+                                              bool rowmaj = false, int Sp = 0) {
   Stager sg;
   sg.vec = contig;
   sg.col = threadIdx.x & (St - 1);
   sg.src0 = sg.src1 = nullptr;
   sg.dst0 = sg.dst1 = 0;
-  if (contig) {
+  sg.rowmaj = rowmaj;
+  sg.Sp = rowmaj ? Sp : St;
+  sg.Ur = 1;
+  sg.r = 0;
+  sg.frow = -1;
+  if (rowmaj) {
+    while (sg.Ur < U) sg.Ur <<= 1;
+    sg.r = threadIdx.x & (sg.Ur - 1);
+    sg.frow = sg.r < U ? s_rowfeat[sg.r] : -1;
+  } else if (contig) {
     const int lq = __ffs(St) - 3;  // log2(St / 4)
     const int total = U << lq;
     const int64_t sid0 = idx[it.beg];
@@ -312,13 +326,24 @@ __device__ __forceinline__ Stager stager_init(const DatasetView& ds, const int32
 }
 
 // Issues the copies of tile t into buf.  A full tile of an aligned run of
-// consecutive samples takes the vector form; any other tile gathers, columns
-// past the item's end repeating its first sample.
+// consecutive samples takes the vector form; the row-major form reads each
+// sample's features from its row of the row-major copy (consecutive threads,
+// consecutive features of one sample), into rows of stride Sp = St + 4 so
+// that those threads' shared-memory writes spread over the banks; any other
+// tile gathers one value per (sample, feature) from the column-major matrix.
+// Columns past the item's end repeat its first sample.
 __device__ __forceinline__ void stager_issue(const Stager& sg, const DatasetView& ds, const int32_t* __restrict__ idx,
                                              const ItemPos& it, int t, int St, int U, const int64_t* s_rowoff,
                                              float* buf) {
   const int64_t nb = it.beg + (int64_t)t * St;
-  if (sg.vec && it.end - nb >= St) {
+  if (sg.rowmaj) {
+    const int spp = kStThreads / sg.Ur;  // sample columns per pass
+    for (int i = threadIdx.x / sg.Ur; i < St; i += spp) {
+      const int64_t pos = nb + i;
+      const int64_t sid = safe_sample(idx[pos < it.end ? pos : nb], ds.n);
+      if (sg.frow >= 0) cp_async4(buf + sg.r * sg.Sp + i, ds.Xr + sid * ds.d + sg.frow);
+    }
+  } else if (sg.vec && it.end - nb >= St) {
     const int64_t o = (int64_t)t * St;
     if (sg.src0) cp_async16(buf + sg.dst0, sg.src0 + o);
     if (sg.src1) cp_async16(buf + sg.dst1, sg.src1 + o);
@@ -346,6 +371,15 @@ __device__ __forceinline__ int choose_st(int U) {
   // U * St <= kTileF, St in {64, 128, 256}
   if (U * 256 <= kTileF) return 256;
   if (U * 128 <= kTileF) return 128;
+  return 64;
+}
+
+// Tile width of the row-major form, whose rows have stride St + 4:
+// U * (St + 4) <= kTileF (U <= kRowMajUMax).
+constexpr int kRowMajUMax = kMmUMax;  // 120 rows at St = 64
+__device__ __forceinline__ int choose_st_pad(int U) {
+  if (U * 260 <= kTileF) return 256;
+  if (U * 132 <= kTileF) return 128;
   return 64;
 }
 
@@ -565,7 +599,7 @@ __device__ __forceinline__ void tile_labels(unsigned lab, int lane, int (&yo)[V 
 // projection live in shared memory (only this warp touches them).
 template <int V, int NQ>
 __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
-                                        int U, bool contig, float* s_tile, const int* s_rowfeat,
+                                        int U, bool contig, bool rowmaj, int Sp, float* s_tile, const int* s_rowfeat,
                                         const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk,
                                         const uint32_t* s_dpk, int kmax, float* s_pmin, float* s_pmax, int lane,
                                         int warp, float* vbuf, int64_t n_total) {
@@ -578,7 +612,7 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
     s_pmin[pl * 32 + lane] = INFINITY;
     s_pmax[pl * 32 + lane] = -INFINITY;
   }
-  const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig);
+  const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig, rowmaj, Sp);
   if (ntile > 0) stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
   cp_async_commit();
   if (ntile > 1) stager_issue(sg, ds, idx, it, 1, St, U, s_rowoff, s_tile + kTileF);
@@ -649,23 +683,33 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
     const ItemPos it = decode_item(sp, t, P);
     const int64_t qbase = (int64_t)it.j * P + it.p0;
     __syncthreads();  // previous item done with shared memory
+    const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
     const int U = build_rows(pv, qbase, it.np, ds.d, s_bits, s_wpre, s_rowfeat, s_misc);
-    const int St = choose_st(U);
-    build_desc<KMAX>(pv, qbase, it.np, ds.d, St, s_bits, s_wpre, s_dk, s_dpk);
+    // scattered samples whose rows are short enough: read the feature rows
+    // from the row-major copy (a row of d <= 8 U floats costs fewer DRAM
+    // sectors than U separate gathers)
+    bool rowmaj = false;
+    if (ds.Xr && !contig && U <= kRowMajUMax && ds.d <= 8 * U) {
+      const int64_t span = (int64_t)idx[it.end - 1] - (int64_t)idx[it.beg];
+      rowmaj = span < 0 || span > 4 * (it.end - it.beg);
+    }
+    const int St = rowmaj ? choose_st_pad(U) : choose_st(U);
+    const int Sp = rowmaj ? St + 4 : St;  // row stride of the tile in shared memory
+    build_desc<KMAX>(pv, qbase, it.np, ds.d, Sp, s_bits, s_wpre, s_dk, s_dpk);
     __syncthreads();  // s_dk and s_rowfeat complete
     for (int r = threadIdx.x; r < U && r < kStUMax; r += kStThreads) s_rowoff[r] = (int64_t)s_rowfeat[r] * ds.ld;
     const int nslot = assign_snake(it.np, s_dk, s_kcnt, s_assign);
-    const bool contig = item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
+    __syncthreads();  // assignment and row offsets visible
     if (U <= kMmUMax) {
       if (St == 256)
-        mm_item<4, 2>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
-                   lane, warp, vbuf, n_total);
+        mm_item<4, 2>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk,
+                      KMAX, s_pmin, s_pmax, lane, warp, vbuf, n_total);
       else if (St == 128)
-        mm_item<4, 1>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
-                   lane, warp, vbuf, n_total);
+        mm_item<4, 1>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk,
+                      KMAX, s_pmin, s_pmax, lane, warp, vbuf, n_total);
       else
-        mm_item<2, 1>(ds, idx, it, U, contig, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_pmin, s_pmax,
-                   lane, warp, vbuf, n_total);
+        mm_item<2, 1>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk,
+                      KMAX, s_pmin, s_pmax, lane, warp, vbuf, n_total);
     } else {
       // direct path for wide groups: each warp gathers its projections' features
       for (int pl = warp; pl < it.np; pl += kStWarps) {

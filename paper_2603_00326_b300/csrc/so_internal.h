@@ -29,6 +29,7 @@ struct DatasetView {
   const uint8_t* y;
   int32_t d;
   int32_t C;
+  const float* Xr = nullptr;  // optional row-major copy [n][d]
 };
 
 // Projection rows q = node*P + p: features feat[beg[q] .. end[q]).

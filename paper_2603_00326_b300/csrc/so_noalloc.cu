@@ -107,6 +107,7 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   a.ds.y = ds->y;
   a.ds.d = ds->d;
   a.ds.C = C;
+  a.ds.Xr = ds->Xr;
   a.idx = idx;
   a.n_total = n_node;
   a.node_off = off;

@@ -28,7 +28,7 @@ class SoError(RuntimeError):
 # ---------------------------------------------------------------- C structs
 class so_dataset(C.Structure):
     _fields_ = [("X", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("ld", C.c_int64),
-                ("y", C.c_void_p), ("n_classes", C.c_int32)]
+                ("y", C.c_void_p), ("n_classes", C.c_int32), ("Xr", C.c_void_p)]
 
 
 class so_projs(C.Structure):
@@ -104,6 +104,7 @@ _SIGS = {
     "so_tree_free": (None, [C.POINTER(so_tree)]),
     "so_autotune": (_I32, [C.POINTER(so_dataset), _I32, _D, _I32, C.POINTER(so_split_params), _V, _V, _V, _V]),
     "so_predict": (_I32, [_V, _I64, _I32, _I64, C.POINTER(so_forest), _V, _V, _V]),
+    "so_row_major": (_I32, [_V, _I64, _I32, _I64, _V, _V]),
     "so_last_error": (C.c_char_p, []),
     "so_shutdown": (None, []),
     "so_version": (C.c_char_p, []),
@@ -148,17 +149,33 @@ def _ptr(t) -> C.c_void_p:
 # ---------------------------------------------------------------- wrappers
 @dataclasses.dataclass
 class DeviceDataset:
-    """X: cuda float32 [d, n] (row f holds feature f), y: cuda uint8 [n]."""
+    """X: cuda float32 [d, n] (row f holds feature f), y: cuda uint8 [n].
+    Xr: optional cuda float32 [n, d], the same values row-major (see
+    with_row_major); used to read scattered samples' feature rows."""
     X: "object"
     y: "object"
     n_classes: int
+    Xr: "object" = None
 
     def c(self) -> so_dataset:
         X = self.X
         assert X.is_cuda and X.dtype.__str__() == "torch.float32" and X.dim() == 2
         assert X.stride(1) == 1
+        xr = 0
+        if self.Xr is not None:
+            assert self.Xr.is_cuda and tuple(self.Xr.shape) == (X.shape[1], X.shape[0]) and self.Xr.is_contiguous()
+            xr = self.Xr.data_ptr()
         return so_dataset(X.data_ptr(), X.shape[1], X.shape[0], X.stride(0), self.y.data_ptr(),
-                          self.n_classes)
+                          self.n_classes, xr)
+
+    def with_row_major(self, stream=None) -> "DeviceDataset":
+        """The same dataset with a row-major copy of X on the device (so_row_major)."""
+        import torch
+        X = self.X
+        Xr = torch.empty((X.shape[1], X.shape[0]), dtype=torch.float32, device=X.device)
+        _check(lib().so_row_major(X.data_ptr(), X.shape[1], X.shape[0], X.stride(0), Xr.data_ptr(),
+                                  _stream(stream)))
+        return DeviceDataset(self.X, self.y, self.n_classes, Xr)
 
 
 @dataclasses.dataclass

@@ -6,8 +6,8 @@ leaves) re-searched by the oracle from its own projection sampler; then the
 tree's predictions for 50,000 rows against the oracle's traversal.
 
 * forest_2m: n=2M, d=256 lognormal features, 8-sparse median-centred labels
-  with 10% flips, bootstrap root, 128 projections/node, T=1024 -- tree 0 of
-  the forest the benchmark times;
+  with 10% flips, bootstrap root, 128 projections/node, T=1024, with the
+  row-major feature copy -- tree 0 of the forest the benchmark times;
 * wide_counts: n=500k, d=4096, 90% zeros, zero-truncated Poisson(3)
   nonzeros, 5 classes, 128 projections/node with 1+Poisson(3) nonzeros
   (cap 16), T=1024, grown to purity.
@@ -30,8 +30,10 @@ def S():
     return soforest
 
 
-def _grow_and_check(S, ds_np, root, p, seed, tree_id, n_internal):
+def _grow_and_check(S, ds_np, root, p, seed, tree_id, n_internal, row_major=False):
     ds = U.upload_dataset(ds_np.X, ds_np.y, ds_np.n_classes)
+    if row_major:
+        ds = ds.with_row_major()
     tp = S.tree_params(p["n_proj"], p["lam"], p["cap"], p["n_bins"], p["sort_below"], False, seed, tree_id, -1)
     gt = S.so_train_tree(ds, U.i32(root), tp)
     # inference with the full-size tree on a sample of rows
@@ -55,7 +57,7 @@ def test_forest_2m_tree_full_size(S):
     cfg = F.ForestConfig(n_trees=p["n_trees"], n_proj=p["n_proj"], lam=p["lam"], cap=p["cap"],
                          sort_below=p["sort_below"])
     root = F.root_indices(ds_np.n, 0, cfg)
-    gt = _grow_and_check(S, ds_np, root, p, cfg.seed, 0, n_internal=16)
+    gt = _grow_and_check(S, ds_np, root, p, cfg.seed, 0, n_internal=16, row_major=True)
     assert set(np.unique(gt.path)) >= {0, 1}
 
 

@@ -409,12 +409,17 @@ def test_autotune_crossover_and_tree_with_tuned_T(S):
 
 # ---------------------------------------------------------------- forest
 
-def test_forest_bootstrap_trees_match_oracle(S):
+@pytest.mark.parametrize("row_major", [False, True])
+def test_forest_bootstrap_trees_match_oracle(S, row_major):
     """A small forest (lognormal heavy-tailed features, 8-sparse median-centred
-    labels, 10% flips): every bootstrapped tree identical to the oracle's."""
+    labels, 10% flips): every bootstrapped tree identical to the oracle's, with
+    and without the row-major copy of the features (scattered samples' rows)."""
     from paper_2603_00326_b300 import forest as F
     ds_np = G.forest_2m(n=6000, d=32, seed=91)
     ds = U.upload_dataset(ds_np.X, ds_np.y, 2)
+    if row_major:
+        ds = ds.with_row_major()
+        np.testing.assert_array_equal(ds.Xr.cpu().numpy(), ds_np.X.T)
     cfg = F.ForestConfig(n_trees=4, n_proj=16, lam=1.5, cap=8, sort_below=512)
     trees, _ = F.train_forest(cfg, ds)
     assert len(trees) == 4
