@@ -156,7 +156,7 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
     ptr = np.concatenate(ptrs).astype(np.int32)
     feat = np.concatenate([q.feat for q in projs]).astype(np.int32)
     sign = np.concatenate([q.sign for q in projs]).astype(np.int8)
-    dd = S.DeviceDataset(torch.from_numpy(ds_np.X).to(dev), torch.from_numpy(ds_np.y).to(dev), 2)
+    dd = S.DeviceDataset(torch.from_numpy(ds_np.X).to(dev), torch.from_numpy(ds_np.y).to(dev), 2).with_row_major()
     cap = int(p["cap"])
     pj = S.DeviceProjs(P, torch.from_numpy(ptr).to(dev), torch.from_numpy(feat).to(dev),
                        torch.from_numpy(sign).to(dev), cap)

@@ -369,8 +369,9 @@ def test_root_4m_full_size(S):
 
 def test_frontier_1m_full_size(S):
     """4096 frontier nodes with lognormal(5, 2) sizes over n=1M, d=128, 64
-    projections/node, mixed exact and histogram paths in one call; every node
-    compared with the oracle."""
+    projections/node, mixed exact and histogram paths in one call, with the
+    row-major feature copy as the benchmark runs it; every node compared with
+    the oracle."""
     ds_np = G.frontier_1m()
     p = G.WORKLOAD_PARAMS["frontier_1m"]
     idx, off = G.frontier_nodes(ds_np.n, p["n_nodes"])
@@ -378,7 +379,7 @@ def test_frontier_1m_full_size(S):
     m, P = p["n_nodes"], p["n_proj"]
     projs = [G.random_projections(rng, P, ds_np.d, p["lam"], p["cap"]) for _ in range(m)]
     ptr, feat, sign = U.concat_projs([(q.ptr, q.feat, q.sign) for q in projs])
-    ds = U.upload_dataset(ds_np.X, ds_np.y, 2)
+    ds = U.upload_dataset(ds_np.X, ds_np.y, 2).with_row_major()
     pj = U.upload_projs(ptr, feat, sign, P)
     prm = S.split_params(256, p["sort_below"], False)
     out, lc = S.so_split_search_batch(ds, U.i32(idx), U.i64(off), pj, prm)
