@@ -425,7 +425,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (histogram fill)
     # DRAM bytes (read + write) of one k_hist_staged launch on this workload, from the ncu capture
     # summarised in profiles/k_hist_staged_root_4m.md; set to None whenever that kernel changes.
-    K_HIST_TRAFFIC_BYTES = 1_099_905_000 + 7_710_208
+    K_HIST_TRAFFIC_BYTES = 1_100_073_000 + 7_715_840
     hbm, peak_kind = peaks()
     used_feats = np.unique(pr.feat).size
     alg_bytes = used_feats * n * 4 + n * 4 + n * 1  # feature columns + index list + labels, one pass
@@ -449,8 +449,8 @@ def run_ours(args):
                      "traffic": K_HIST_TRAFFIC_BYTES if WORKLOAD == "root_4m" else None,
                      "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                      "avg_launch_ms": k_avg_ms,
-                     "limit": "shared-memory atomics and instruction issue, not HBM (ncu: issue 78% busy, "
-                              "DRAM 9% of peak)"},
+                     "limit": "shared-memory atomics, shared-memory latency and instruction issue, not HBM "
+                              "(ncu: issue 66% busy, shared-memory pipe 63%, DRAM 9% of peak)"},
         "stage_ms_per_launch": stage_ms,
         "clocks": clk,
         "split": {"proj": int(rec["proj"]), "cand": int(rec["cand"]), "gain": float(rec["gain"]),
