@@ -137,7 +137,8 @@ def cpu_baseline(ds, pr, n_sample_proj: int, threads: int = 1):
 def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
-    64 projections/node, T=1024), and one tree grown to purity (tree_small)."""
+    64 projections/node, crossover T autotuned), one tree grown to purity
+    (tree_small), trees of the forest (forest_2m) and the wide tree."""
     from paper_2603_00326_b300 import datagen as G
     out = {}
     if only not in (None, "frontier"):
@@ -162,7 +163,9 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
                        torch.from_numpy(sign).to(dev), cap)
     idx = torch.from_numpy(idx_np).to(dev)
     off = torch.from_numpy(off_np).to(dev)
-    prm = S.split_params(256, p["sort_below"], False)
+    # the crossover T from the start-up microbenchmark (Section 3.1), as this
+    # workload specifies; both forms below use it
+    prm, tune_sizes, tune_ms = S.so_autotune(dd, P, p["lam"], int(p["cap"]), S.split_params(256, p["sort_below"], False))
     ws = torch.empty(S.so_split_search_ws_bytes(m, ds_np.n, P, 2, prm), dtype=torch.uint8, device=dev)
     outb = torch.empty(m * S.SPLIT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     for _ in range(3):
@@ -195,7 +198,8 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
     same = all(int(rec[j]["proj"]) == plain[j].proj and int(rec[j]["cand"]) == plain[j].cand and
                float(rec[j]["gain"]) == plain[j].gain for j in range(m))
     sp = float(ds_np.n * P)
-    out["frontier_1m"] = {"nodes": m, "batched_ms": batched_ms, "plain_ms": plain_ms,
+    out["frontier_1m"] = {"nodes": m, "autotuned_sort_below": int(prm.sort_below),
+                          "batched_ms": batched_ms, "plain_ms": plain_ms,
                           "speedup": plain_ms / batched_ms, "identical": bool(same),
                           "batched_sample_projections_per_s": sp / (batched_ms / 1000.0)}
     del dd, idx, off, ws, outb, views

@@ -854,8 +854,12 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
     int32_t mcap = 1;
     for (int si = 0; si < n_sizes; ++si) mcap = std::max<int32_t>(mcap, nodes_for(kSizes[si]));
     const int64_t ncap = (int64_t)mcap * kSizes[n_sizes - 1] + budget;
+    // projected-value buffer of the histogram path, as batched calls use it
+    int64_t max_nt = 0;
+    for (int si = 0; si < n_sizes; ++si) max_nt = std::max<int64_t>(max_nt, (int64_t)nodes_for(kSizes[si]) * kSizes[si]);
     auto layout = [&](Carver& cv, int32_t** idx, int64_t** off, uint64_t** keys, int32_t** snnz, int32_t** sbeg,
-                      int32_t** send, int32_t** sfeat, int8_t** ssign, so_split** out, SearchScratch* ss) {
+                      int32_t** send, int32_t** sfeat, int8_t** ssign, so_split** out, SearchScratch* ss,
+                      float** vbuf) {
       *idx = cv.take<int32_t>(ncap);
       *off = cv.take<int64_t>(mcap + 1);
       *keys = cv.take<uint64_t>(mcap);
@@ -866,6 +870,7 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
       *ssign = cv.take<int8_t>((size_t)mcap * P * cap);
       *out = cv.take<so_split>(mcap);
       carve_search(cv, *ss, mcap, ncap, P, C, B, kMaxSortBelow, 1);  // histogram scratch for every node
+      *vbuf = cv.take<float>((size_t)P * (size_t)max_nt);
     };
     int32_t *idx, *snnz, *sbeg, *send, *sfeat;
     int64_t* off;
@@ -873,15 +878,16 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
     int8_t* ssign;
     so_split* out;
     SearchScratch ss;
+    float* vbuf = nullptr;
     Carver dry;
     dry.dry = true;
-    layout(dry, &idx, &off, &keys, &snnz, &sbeg, &send, &sfeat, &ssign, &out, &ss);
+    layout(dry, &idx, &off, &keys, &snnz, &sbeg, &send, &sfeat, &ssign, &out, &ss, &vbuf);
     ArenaLease lease;
     if ((st = lease.acquire(dry.used + 4096, cs))) return st;
     Carver cv;
     cv.base = (char*)lease.ptr();
     cv.cap = lease.cap();
-    layout(cv, &idx, &off, &keys, &snnz, &sbeg, &send, &sfeat, &ssign, &out, &ss);
+    layout(cv, &idx, &off, &keys, &snnz, &sbeg, &send, &sfeat, &ssign, &out, &ss, &vbuf);
     if (!cv.ok()) return fail(SO_ENOMEM, "arena too small");
     cudaEvent_t e0, e1;
     SO_CK(cudaEventCreate(&e0));
@@ -909,6 +915,7 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
         a.max_nnz = cap;
         a.out = out;
         a.left_counts = nullptr;
+        a.vbuf = m > 1 ? vbuf : nullptr;
         SO_CK(launch_search(a, ss, cs));  // warm-up
         SO_CK(cudaEventRecord(e0, cs));
         const int reps = 3;

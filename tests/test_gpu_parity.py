@@ -370,8 +370,8 @@ def test_root_4m_full_size(S):
 def test_frontier_1m_full_size(S):
     """4096 frontier nodes with lognormal(5, 2) sizes over n=1M, d=128, 64
     projections/node, mixed exact and histogram paths in one call, with the
-    row-major feature copy as the benchmark runs it; every node compared with
-    the oracle."""
+    row-major feature copy and the autotuned crossover T as the benchmark runs
+    it (and at T = 1024); every node compared with the oracle."""
     ds_np = G.frontier_1m()
     p = G.WORKLOAD_PARAMS["frontier_1m"]
     idx, off = G.frontier_nodes(ds_np.n, p["n_nodes"])
@@ -381,14 +381,15 @@ def test_frontier_1m_full_size(S):
     ptr, feat, sign = U.concat_projs([(q.ptr, q.feat, q.sign) for q in projs])
     ds = U.upload_dataset(ds_np.X, ds_np.y, 2).with_row_major()
     pj = U.upload_projs(ptr, feat, sign, P)
-    prm = S.split_params(256, p["sort_below"], False)
-    out, lc = S.so_split_search_batch(ds, U.i32(idx), U.i64(off), pj, prm)
-    rec = S.splits_to_numpy(out)
-    for j in range(m):
-        q = projs[j]
-        r = O.split_search(ds_np.X, ds_np.y, 2, idx[off[j]:off[j + 1]], q.ptr, q.feat, q.sign,
-                           sort_below=p["sort_below"])
-        U.assert_split_equal(rec[j], r, f"node {j}")
+    tuned, _, _ = S.so_autotune(ds, P, p["lam"], p["cap"], S.split_params(256, p["sort_below"], False))
+    for T in sorted({int(tuned.sort_below), p["sort_below"]}):
+        prm = S.split_params(256, T, False)
+        out, lc = S.so_split_search_batch(ds, U.i32(idx), U.i64(off), pj, prm)
+        rec = S.splits_to_numpy(out)
+        for j in range(m):
+            q = projs[j]
+            r = O.split_search(ds_np.X, ds_np.y, 2, idx[off[j]:off[j + 1]], q.ptr, q.feat, q.sign, sort_below=T)
+            U.assert_split_equal(rec[j], r, f"node {j} T {T}")
 
 
 # ---------------------------------------------------------------- crossover autotune
