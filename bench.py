@@ -208,7 +208,7 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
     return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees)
 
 
-def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1):
+def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_trees=1):
     from paper_2603_00326_b300 import datagen as G
     if only in (None, "tree"):
         # one tree to purity
@@ -279,6 +279,25 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1):
         out["wide_counts"] = {"train_s": min(times), "trees": wide_trees, "nodes": tr.n_nodes,
                               "depth": int(tr.depth.max())}
         del dd, root
+    if trunk_trees > 0 and only in (None, "trunk"):
+        # the Trunk generator at the paper's 100k and 1M rows, p = 1024: one
+        # tree to purity each (the paper's Trunk rows are 128-tree forests)
+        tp_ = G.WORKLOAD_PARAMS["trunk"]
+        res = {}
+        for n_tr in (100_000, 1_000_000):
+            tk = G.trunk(n=n_tr, p=1024)
+            dd = S.DeviceDataset(torch.from_numpy(tk.X).to(dev), torch.from_numpy(tk.y).to(dev), 2).with_row_major()
+            root = torch.from_numpy(G.all_indices(tk.n)).to(dev)
+            prm = S.tree_params(tp_["n_proj"], tp_["lam"], tp_["cap"], tp_["n_bins"], tp_["sort_below"],
+                                seed=G.PROJ_SEED_BASE + 5)
+            S.so_train_tree(dd, root, S.tree_params(8, 1.0, 8, 256, 1024, seed=1, max_depth=3))  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tr = S.so_train_tree(dd, root, prm)
+            res[f"trunk_{n_tr // 1000}k"] = {"train_s": time.perf_counter() - t0, "nodes": tr.n_nodes,
+                                             "depth": int(tr.depth.max())}
+            del dd, root, tk
+        out["trunk_p1024"] = res
     torch.cuda.empty_cache()
     return out
 
@@ -487,7 +506,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the frontier, tree and forest legs")
-    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest", "wide"],
+    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest", "wide", "trunk"],
                     help="run one secondary leg alone and print its JSON")
     ap.add_argument("--forest-trees", type=int, default=2,
                     help="trees of the n=2M, d=256 forest timed in the extras (0 skips)")

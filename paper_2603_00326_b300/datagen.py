@@ -18,6 +18,10 @@ not available offline, so five synthetic workloads shaped like them stand in:
 * ``forest_2m``     n=2M, d=256, lognormal(0,1) features, 128 bootstrapped
                     trees, 128 projections/node.
 * ``wide_counts``   n=500k, d=4096, 90% zeros, Poisson(3) nonzeros, 5 classes.
+* ``trunk``         the Trunk generator of the paper's Table 1: p-dimensional
+                    Gaussians with class means +mu and -mu, mu_j = 1/sqrt(j),
+                    identity covariance, two balanced classes (a "next" workload
+                    for the paper's Trunk-100k / 1M scaling rows).
 
 Every generator takes the sizes as arguments, so tests draw the same recipe at
 sizes the oracle finishes in seconds.
@@ -210,6 +214,32 @@ def wide_counts(n: int = 500_000, d: int = 4096, seed: int = DATA_SEED_BASE + 4)
     return Dataset(X, y, 5, "wide_counts")
 
 
+def _trunk_block(X: np.ndarray, f0: int, f1: int, sgn: np.ndarray, ss: np.random.SeedSequence) -> None:
+    rng = np.random.default_rng(ss)
+    n = X.shape[1]
+    for f in range(f0, f1):
+        mu = np.float32(1.0 / np.sqrt(f + 1.0))
+        X[f] = rng.standard_normal(n, dtype=np.float32) + sgn * mu
+
+
+def trunk(n: int = 1_000_000, p: int = 1024, seed: int = DATA_SEED_BASE + 5) -> Dataset:
+    """Trunk: exactly balanced classes in a seeded random order; class 0 drawn
+    from N(+mu, I), class 1 from N(-mu, I), mu_j = 1/sqrt(j) for j = 1..p.
+    64-feature blocks draw from child streams of the seed (thread pool)."""
+    from concurrent.futures import ThreadPoolExecutor
+    root = np.random.SeedSequence(seed)
+    children = root.spawn((p + 63) // 64 + 1)
+    y = np.zeros(n, dtype=np.uint8)
+    y[n // 2:] = 1
+    np.random.default_rng(children[-1]).shuffle(y)
+    sgn = np.where(y == 0, np.float32(1.0), np.float32(-1.0)).astype(np.float32)
+    X = np.empty((p, n), dtype=np.float32)
+    starts = list(range(0, p, 64))
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(lambda a: _trunk_block(X, a[0], min(p, a[0] + 64), sgn, a[1]), zip(starts, children[:-1])))
+    return Dataset(X, y, 2, "trunk")
+
+
 def lognormal_node_sizes(rng: np.random.Generator, m: int, n: int,
                          mu: float = 5.0, sigma: float = 2.0) -> np.ndarray:
     """m node sizes ~ lognormal(mu, sigma) rescaled to sum to n (each >= 1)."""
@@ -256,4 +286,7 @@ WORKLOAD_PARAMS = {
     "frontier_1m": dict(n_proj=64, lam=1.5, cap=8, n_bins=256, sort_below=1024, n_nodes=4096),
     "forest_2m": dict(n_proj=128, lam=1.5, cap=8, n_bins=256, sort_below=1024, n_trees=128),
     "wide_counts": dict(n_proj=128, lam=3.0, cap=16, n_bins=256, sort_below=1024),
+    # P = 1.5 sqrt(p) projections of about 2 non-zeros each (3 sqrt(p) non-zeros
+    # in all, the paper's Section 3 density) for p = 1024
+    "trunk": dict(n_proj=48, lam=1.0, cap=8, n_bins=256, sort_below=1024),
 }

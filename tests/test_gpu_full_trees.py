@@ -10,7 +10,9 @@ tree's predictions for 50,000 rows against the oracle's traversal.
   row-major feature copy -- tree 0 of the forest the benchmark times;
 * wide_counts: n=500k, d=4096, 90% zeros, zero-truncated Poisson(3)
   nonzeros, 5 classes, 128 projections/node with 1+Poisson(3) nonzeros
-  (cap 16), T=1024, grown to purity.
+  (cap 16), T=1024, grown to purity;
+* trunk: n=1M, p=1024 Trunk Gaussians, 48 projections/node of 1+Poisson(1)
+  nonzeros, T=1024, grown to purity.
 """
 import numpy as np
 import pytest
@@ -66,4 +68,12 @@ def test_wide_counts_tree_full_size(S):
     p = G.WORKLOAD_PARAMS["wide_counts"]
     root = G.all_indices(ds_np.n)
     gt = _grow_and_check(S, ds_np, root, p, G.PROJ_SEED_BASE + 4, 0, n_internal=16)
+    assert set(np.unique(gt.path)) >= {0, 1}
+
+
+def test_trunk_1m_tree_full_size(S):
+    ds_np = G.trunk(n=1_000_000, p=1024)
+    p = G.WORKLOAD_PARAMS["trunk"]
+    root = G.all_indices(ds_np.n)
+    gt = _grow_and_check(S, ds_np, root, p, G.PROJ_SEED_BASE + 5, 0, n_internal=12, row_major=True)
     assert set(np.unique(gt.path)) >= {0, 1}

@@ -312,7 +312,7 @@ def test_tree_parity_tree_small_full(S):
 
 
 @pytest.mark.parametrize("variant", ["multiclass_bootstrap", "hist_only_b32", "max_depth", "counts_ties",
-                                     "tiny_T"])
+                                     "tiny_T", "trunk"])
 def test_tree_parity_variants(S, variant):
     rng = np.random.default_rng(hash(variant) % 1000)
     if variant == "multiclass_bootstrap":
@@ -331,6 +331,10 @@ def test_tree_parity_variants(S, variant):
         ds = G.wide_counts(n=4000, d=256, seed=96)
         root = G.all_indices(ds.n)
         kw = dict(n_proj=32, lam=3.0, cap=16, sort_below=1024, seed=8)
+    elif variant == "trunk":
+        ds = G.trunk(n=6000, p=64, seed=94)
+        root = G.all_indices(ds.n)
+        kw = dict(n_proj=12, lam=1.0, cap=8, sort_below=700, seed=10)
     else:
         ds = G.tree_small(n=4000, d=16, seed=95)
         root = G.all_indices(ds.n)
