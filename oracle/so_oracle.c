@@ -47,6 +47,13 @@
  *   R7 tree: breadth-first node order, children appended left then right.
  *      Node keys and projection streams use splitmix64 (Steele, Lea & Flood,
  *      OOPSLA 2014); nnz = min(cap, d, 1 + Poisson(lambda)) by inverse CDF.
+ *   R14 random-width histogram (the YDF default the paper's Section 1 footnote
+ *      names: boundaries at random intervals): for node key K and projection
+ *      p, a splitmix64 generator with state sm64((K ^ BIN_TAG) + p*PROJ_MULT)
+ *      draws B-1 outputs r_j; u_j = r_j >> 41 (23 bits) sorted ascending;
+ *      f_j = (2 u_j + 1) * 2^-24, exact in float and inside (0, 1);
+ *      t_j = min + f_j * (max - min), float, two roundings.  Bin, candidates
+ *      and thresholds then follow R2 with these t_j.
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,6 +63,8 @@
 
 #define ORC_GAMMA 0x9E3779B97F4A7C15ULL   /* splitmix64 increment (golden ratio) */
 #define ORC_PROJ_MULT 0xD2B74407B1CE6E93ULL /* odd multiplier separating projection streams */
+#define ORC_BIN_TAG 0x6A09E667F3BCC908ULL   /* first 64 fractional bits of sqrt(2): tags the
+                                               boundary streams apart from the projection streams */
 #define ORC_MAX_CLASSES 8
 #define ORC_MAX_CAP 32
 
@@ -216,6 +225,30 @@ void orc_boundaries(float mn, float mx, int B, float *t)
         t[j - 1] = mn + (float)j * w;
 }
 
+/* R14: the B-1 random-width boundaries of projection p of the node with key
+ * `key` (t[j-1] holds t_j, ascending). */
+void orc_rw_boundaries(uint64_t key, int p, float mn, float mx, int B, float *t)
+{
+    uint32_t u[256];
+    uint64_t st = orc_sm64((key ^ ORC_BIN_TAG) + (uint64_t)(int64_t)p * ORC_PROJ_MULT);
+    for (int j = 0; j < B - 1; j++)
+        u[j] = (uint32_t)(orc_sm64_next(&st) >> 41);
+    for (int a = 1; a < B - 1; a++) { /* insertion sort, ascending */
+        uint32_t v = u[a];
+        int b = a - 1;
+        while (b >= 0 && u[b] > v) {
+            u[b + 1] = u[b];
+            b--;
+        }
+        u[b + 1] = v;
+    }
+    float w = mx - mn;
+    for (int j = 0; j < B - 1; j++) {
+        float f = (float)(2u * u[j] + 1u) * 0x1p-24f;
+        t[j] = mn + f * w;
+    }
+}
+
 /* R2: bin = number of boundaries <= v, found by a textbook upper-bound
  * binary search over the non-decreasing array t[0..nb-1]. */
 int orc_bin(const float *t, int nb, float v)
@@ -256,6 +289,9 @@ float orc_midpoint(float a, float b)
 /*
  * Best split of one node over P projections (CSR ptr/feat/sign).
  * Path: exact sort if !hist_only && n < sort_below, else histogram.
+ * bin_rule 0: equal-width boundaries (R2); 1: random-width (R14) from the
+ * node's key bin_key, projection p drawing from stream p_base + p (p_base is
+ * nonzero only when a caller searches a sub-range of the node's projections).
  * Optional outputs (may be NULL):
  *   left_counts[C]   class counts of the chosen left child
  *   mm_out[2P]       per projection (min, max)            (histogram path)
@@ -264,16 +300,18 @@ float orc_midpoint(float a, float b)
  *   best32_out[P]    unused by the oracle (kept NULL)
  * Returns 0, or -1 on a bad argument / allocation failure.
  */
-int orc_split_search(const float *X, int64_t ld, const uint8_t *y, int C,
-                     const int32_t *idx, int64_t n, int P, const int32_t *ptr,
-                     const int32_t *feat, const int8_t *sign, int B, int sort_below,
-                     int hist_only, orc_split *out, int64_t *left_counts,
-                     float *mm_out, int32_t *hist_out, double *gains_out)
+int orc_split_search_rule(const float *X, int64_t ld, const uint8_t *y, int C,
+                          const int32_t *idx, int64_t n, int P, const int32_t *ptr,
+                          const int32_t *feat, const int8_t *sign, int B, int sort_below,
+                          int hist_only, int bin_rule, uint64_t bin_key, int p_base,
+                          orc_split *out, int64_t *left_counts, float *mm_out,
+                          int32_t *hist_out, double *gains_out, float *bounds_out)
 {
     memset(out, 0, sizeof(*out));
     out->proj = -1;
     out->cand = -1;
-    if (C < 1 || C > ORC_MAX_CLASSES || B < 2 || B > 256 || n < 0 || P < 0)
+    if (C < 1 || C > ORC_MAX_CLASSES || B < 2 || B > 256 || n < 0 || P < 0 ||
+        bin_rule < 0 || bin_rule > 1)
         return -1;
     int64_t N[ORC_MAX_CLASSES] = {0};
     for (int64_t i = 0; i < n; i++)
@@ -336,7 +374,12 @@ int orc_split_search(const float *X, int64_t ld, const uint8_t *y, int C,
                 mm_out[2 * p] = mn;
                 mm_out[2 * p + 1] = mx;
             }
-            orc_boundaries(mn, mx, B, t);
+            if (bin_rule == 1)
+                orc_rw_boundaries(bin_key, p_base + p, mn, mx, B, t);
+            else
+                orc_boundaries(mn, mx, B, t);
+            if (bounds_out)
+                memcpy(bounds_out + (int64_t)p * (B - 1), t, (size_t)(B - 1) * sizeof(float));
             memset(H, 0, (size_t)B * C * sizeof(int64_t));
             for (int64_t i = 0; i < n; i++) {
                 int b = orc_bin(t, B - 1, v[i]);
@@ -377,6 +420,18 @@ int orc_split_search(const float *X, int64_t ld, const uint8_t *y, int C,
             left_counts[c] = bestL[c];
     free(v); free(pairs); free(H); free(t);
     return 0;
+}
+
+/* The search with equal-width boundaries (R2). */
+int orc_split_search(const float *X, int64_t ld, const uint8_t *y, int C,
+                     const int32_t *idx, int64_t n, int P, const int32_t *ptr,
+                     const int32_t *feat, const int8_t *sign, int B, int sort_below,
+                     int hist_only, orc_split *out, int64_t *left_counts,
+                     float *mm_out, int32_t *hist_out, double *gains_out)
+{
+    return orc_split_search_rule(X, ld, y, C, idx, n, P, ptr, feat, sign, B, sort_below,
+                                 hist_only, 0, 0, 0, out, left_counts, mm_out, hist_out,
+                                 gains_out, NULL);
 }
 
 /* R6: stable partition of idx[0..n) by v < thr; returns the left count. */
@@ -453,7 +508,7 @@ static int tree_reserve(orc_tree *t, int64_t cap_nodes, int C, int cap)
  */
 int orc_train_tree(const float *X, int64_t ld, int32_t d, const uint8_t *y, int C,
                    const int32_t *root_idx, int64_t n_root, int B, int sort_below,
-                   int hist_only, int P, double lambda, int cap, uint64_t seed,
+                   int hist_only, int bin_rule, int P, double lambda, int cap, uint64_t seed,
                    int32_t tree_id, int32_t max_depth, orc_tree *out)
 {
     memset(out, 0, sizeof(*out));
@@ -531,8 +586,9 @@ int orc_train_tree(const float *X, int64_t ld, int32_t d, const uint8_t *y, int 
                 ptr[p + 1] = ptr[p] + pnnz[p];
             }
             orc_split sp;
-            if (orc_split_search(X, ld, y, C, seg, nd.cnt, P, ptr, cfeat, csign, B, sort_below,
-                                 hist_only, &sp, NULL, NULL, NULL, NULL))
+            if (orc_split_search_rule(X, ld, y, C, seg, nd.cnt, P, ptr, cfeat, csign, B,
+                                      sort_below, hist_only, bin_rule, nd.key, 0, &sp, NULL,
+                                      NULL, NULL, NULL, NULL))
                 goto done;
             out->path[id] = (int8_t)sp.path;
             if (!sp.valid)
@@ -618,23 +674,25 @@ void orc_predict_tree(const orc_tree *t, const float *X, int64_t ld, const int32
 typedef struct {
     const float *X; int64_t ld; const uint8_t *y; int C; const int32_t *idx; int64_t n;
     int p0, p1; const int32_t *ptr; const int32_t *feat; const int8_t *sign;
-    int B, sort_below, hist_only;
+    int B, sort_below, hist_only, bin_rule; uint64_t bin_key;
     orc_split res; int64_t lc[ORC_MAX_CLASSES]; int rc;
 } orc_range_job;
 
 static void *orc_range_run(void *arg)
 {
     orc_range_job *j = (orc_range_job *)arg;
-    j->rc = orc_split_search(j->X, j->ld, j->y, j->C, j->idx, j->n, j->p1 - j->p0, j->ptr + j->p0,
-                             j->feat, j->sign, j->B, j->sort_below, j->hist_only, &j->res, j->lc,
-                             NULL, NULL, NULL);
+    j->rc = orc_split_search_rule(j->X, j->ld, j->y, j->C, j->idx, j->n, j->p1 - j->p0,
+                                  j->ptr + j->p0, j->feat, j->sign, j->B, j->sort_below,
+                                  j->hist_only, j->bin_rule, j->bin_key, j->p0, &j->res, j->lc,
+                                  NULL, NULL, NULL, NULL);
     return NULL;
 }
 
 int orc_split_search_mt(const float *X, int64_t ld, const uint8_t *y, int C,
                         const int32_t *idx, int64_t n, int P, const int32_t *ptr,
                         const int32_t *feat, const int8_t *sign, int B, int sort_below,
-                        int hist_only, int n_threads, orc_split *out, int64_t *left_counts)
+                        int hist_only, int bin_rule, uint64_t bin_key, int n_threads,
+                        orc_split *out, int64_t *left_counts)
 {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > P) n_threads = P > 0 ? P : 1;
@@ -648,6 +706,7 @@ int orc_split_search_mt(const float *X, int64_t ld, const uint8_t *y, int C,
         j->p1 = (int)((int64_t)P * (t + 1) / n_threads);
         j->ptr = ptr; j->feat = feat; j->sign = sign;
         j->B = B; j->sort_below = sort_below; j->hist_only = hist_only;
+        j->bin_rule = bin_rule; j->bin_key = bin_key;
     }
     int started = 0;
     for (int t = 1; t < n_threads; t++) {

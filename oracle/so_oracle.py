@@ -44,6 +44,14 @@ def lib():
         L.orc_gini_gain.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_int64]
         L.orc_boundaries.restype = None
         L.orc_boundaries.argtypes = [C.c_float, C.c_float, C.c_int, C.c_void_p]
+        L.orc_rw_boundaries.restype = None
+        L.orc_rw_boundaries.argtypes = [C.c_uint64, C.c_int, C.c_float, C.c_float, C.c_int, C.c_void_p]
+        L.orc_split_search_rule.restype = C.c_int
+        L.orc_split_search_rule.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
+                                            C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]
         L.orc_bin.restype = C.c_int
         L.orc_bin.argtypes = [C.c_void_p, C.c_int, C.c_float]
         L.orc_midpoint.restype = C.c_float
@@ -59,14 +67,15 @@ def lib():
         L.orc_train_tree.restype = C.c_int
         L.orc_train_tree.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int,
                                      C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
-                                     C.c_double, C.c_int, C.c_uint64, C.c_int32, C.c_int32,
+                                     C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int32, C.c_int32,
                                      C.c_void_p]
         L.orc_tree_free.restype = None
         L.orc_tree_free.argtypes = [C.c_void_p]
         L.orc_split_search_mt.restype = C.c_int
         L.orc_split_search_mt.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
                                           C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
-                                          C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+                                          C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                                          C.c_void_p, C.c_void_p]
         L.orc_predict_tree.restype = None
         L.orc_predict_tree.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                        C.c_int64, C.c_void_p]
@@ -170,6 +179,13 @@ def boundaries(mn: float, mx: float, B: int) -> np.ndarray:
     return t
 
 
+def rw_boundaries(key: int, p: int, mn: float, mx: float, B: int) -> np.ndarray:
+    """Random-width boundaries t_1..t_{B-1} of projection p at the node with key `key`."""
+    t = np.empty(B - 1, dtype=np.float32)
+    lib().orc_rw_boundaries(C.c_uint64(key & 0xFFFFFFFFFFFFFFFF), p, C.c_float(mn), C.c_float(mx), B, _p(t))
+    return t
+
+
 def bin_of(t: np.ndarray, v: float) -> int:
     t = _c(t, np.float32)
     return int(lib().orc_bin(_p(t), t.shape[0], C.c_float(v)))
@@ -193,12 +209,15 @@ class SplitResult:
     minmax: Optional[np.ndarray] = None     # float32 [P, 2]
     hist: Optional[np.ndarray] = None       # int32 [P, B, C]
     gains: Optional[np.ndarray] = None      # float64 [P, B-1]
+    bounds: Optional[np.ndarray] = None     # float32 [P, B-1] boundaries t_1..t_{B-1}
 
 
 def split_search(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
                  ptr: np.ndarray, feat: np.ndarray, sign: np.ndarray, n_bins: int = 256,
                  sort_below: int = 1024, hist_only: bool = False,
-                 want_debug: bool = False) -> SplitResult:
+                 want_debug: bool = False, bin_rule: int = 0, bin_key: int = 0) -> SplitResult:
+    """bin_rule 0: equal-width boundaries; 1: random-width boundaries drawn
+    from the node key bin_key."""
     X = _c(X, np.float32)
     y = _c(y, np.uint8)
     idx = _c(idx, np.int32)
@@ -208,25 +227,28 @@ def split_search(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
     P = ptr.shape[0] - 1
     out = OrcSplit()
     lc = np.zeros(n_classes, dtype=np.int64)
-    mm = hist = gains = None
+    mm = hist = gains = bounds = None
     if want_debug:
         mm = np.zeros((P, 2), dtype=np.float32)
         hist = np.zeros((P, n_bins, n_classes), dtype=np.int32)
         gains = np.full((P, n_bins - 1), -1.0, dtype=np.float64)
-    rc = lib().orc_split_search(
+        bounds = np.zeros((P, n_bins - 1), dtype=np.float32)
+    opt = lambda a: _p(a) if a is not None else None  # noqa: E731
+    rc = lib().orc_split_search_rule(
         _p(X), X.shape[1], _p(y), n_classes, _p(idx), idx.shape[0], P, _p(ptr), _p(feat),
-        _p(sign), n_bins, sort_below, int(bool(hist_only)), C.byref(out), _p(lc),
-        _p(mm) if mm is not None else None, _p(hist) if hist is not None else None,
-        _p(gains) if gains is not None else None)
+        _p(sign), n_bins, sort_below, int(bool(hist_only)), int(bin_rule),
+        C.c_uint64(bin_key & 0xFFFFFFFFFFFFFFFF), 0, C.byref(out), _p(lc), opt(mm), opt(hist),
+        opt(gains), opt(bounds))
     if rc:
-        raise ValueError("orc_split_search failed")
+        raise ValueError("orc_split_search_rule failed")
     return SplitResult(out.valid, out.proj, out.path, out.cand, np.float32(out.threshold),
-                       out.gain, out.n_left, out.n_right, lc, mm, hist, gains)
+                       out.gain, out.n_left, out.n_right, lc, mm, hist, gains, bounds)
 
 
 def split_search_mt(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
                     ptr: np.ndarray, feat: np.ndarray, sign: np.ndarray, n_bins: int = 256,
-                    sort_below: int = 1024, hist_only: bool = False, n_threads: int = 1) -> SplitResult:
+                    sort_below: int = 1024, hist_only: bool = False, n_threads: int = 1,
+                    bin_rule: int = 0, bin_key: int = 0) -> SplitResult:
     """split_search with the projections divided over n_threads host threads
     (same result; no debug outputs)."""
     X = _c(X, np.float32)
@@ -239,7 +261,8 @@ def split_search_mt(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarra
     out = OrcSplit()
     lc = np.zeros(n_classes, dtype=np.int64)
     rc = lib().orc_split_search_mt(_p(X), X.shape[1], _p(y), n_classes, _p(idx), idx.shape[0], P, _p(ptr),
-                                   _p(feat), _p(sign), n_bins, sort_below, int(bool(hist_only)), n_threads,
+                                   _p(feat), _p(sign), n_bins, sort_below, int(bool(hist_only)),
+                                   int(bin_rule), C.c_uint64(bin_key & 0xFFFFFFFFFFFFFFFF), n_threads,
                                    C.byref(out), _p(lc))
     if rc:
         raise ValueError("orc_split_search_mt failed")
@@ -286,14 +309,14 @@ class Tree:
 def train_tree(X: np.ndarray, y: np.ndarray, n_classes: int, root_idx: np.ndarray, *,
                n_proj: int, lam: float, cap: int, n_bins: int = 256, sort_below: int = 1024,
                hist_only: bool = False, seed: int = 0, tree_id: int = 0,
-               max_depth: int = -1) -> Tree:
+               max_depth: int = -1, bin_rule: int = 0) -> Tree:
     X = _c(X, np.float32)
     y = _c(y, np.uint8)
     root_idx = _c(root_idx, np.int32)
     t = OrcTree()
     rc = lib().orc_train_tree(_p(X), X.shape[1], X.shape[0], _p(y), n_classes, _p(root_idx),
                               root_idx.shape[0], n_bins, sort_below, int(bool(hist_only)),
-                              n_proj, lam, cap, C.c_uint64(seed), tree_id, max_depth,
+                              int(bin_rule), n_proj, lam, cap, C.c_uint64(seed), tree_id, max_depth,
                               C.byref(t))
     if rc:
         raise RuntimeError("orc_train_tree failed")
