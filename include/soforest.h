@@ -83,19 +83,40 @@ typedef struct {
                               longer than this marks its node malformed. */
 } so_projs;
 
+/* Histogram boundary rules (so_split_params.bin_rule). */
+enum { SO_BINS_EQUAL_WIDTH = 0, SO_BINS_RANDOM_WIDTH = 1 };
+
 /* Split-search parameters.
- *  n_bins       equal-width bins per projection, 2..256 (Section 3.2 uses 256).
+ *  n_bins       bins per projection, 2..256 (Section 3.2 uses 256).
  *  sort_below   T: nodes with fewer than T samples take the exact sort path
  *               (Section 3.1); 0..2048.
  *  hist_only    nonzero: every node takes the histogram path.
  *  rescore_rel_eps  relative window of the double-precision re-score of
  *               float near-ties; <= 0 selects the default 4e-6.  Values below
- *               the float error bound of the gain are raised to that bound. */
+ *               the float error bound of the gain are raised to that bound.
+ *  bin_rule     where the B-1 boundaries t_1..t_{B-1} of a projection with
+ *               node range [min, max] sit.  Under both rules a value v falls
+ *               in bin #{j : t_j <= v}, candidate b sends bins <= b left
+ *               (exactly v < t_{b+1}) and its threshold is t_{b+1}.
+ *               SO_BINS_EQUAL_WIDTH: t_j = min + j*w, w = (max-min)/B (float).
+ *               SO_BINS_RANDOM_WIDTH: boundaries at random intervals, the
+ *               YDF default the paper's Section 1 footnote names.  For the
+ *               node key K and projection p, a splitmix64 generator with state
+ *               splitmix64((K ^ 0x6A09E667F3BCC908) + p*0xD2B74407B1CE6E93)
+ *               draws B-1 outputs r; their top 23 bits u = r >> 41, sorted
+ *               ascending, place t_j = min + f_j*(max-min) with
+ *               f_j = (2u+1)*2^-24 (float, two roundings).
+ *  bin_keys     SO_BINS_RANDOM_WIDTH: device uint64 [m], the key of each node
+ *               of the call (node j of a batch reads bin_keys[j]; a one-node
+ *               call reads bin_keys[0]); the same keys so_sample_projections
+ *               takes.  Ignored (may be NULL) for equal width. */
 typedef struct {
     int32_t n_bins;
     int32_t sort_below;
     int32_t hist_only;
     float rescore_rel_eps;
+    int32_t bin_rule;
+    const uint64_t *bin_keys;
 } so_split_params;
 
 /* Result of one node's split search.
@@ -218,18 +239,22 @@ so_status so_sample_projections(int32_t m, const uint64_t *keys, int32_t n_proj,
 /* The histogram stage alone for m nodes, every node on the histogram path
  * (Section 3 step 2; the paper's first GPU kernel).  For inspection and
  * testing of the intermediate results.
+ *  params      n_bins, bin_rule and bin_keys are used; the rest is ignored.
  *  minmax_dev  device float [m*n_proj*2]: (min, max) of each projection.
  *  hist_dev    device int32 [m*n_proj*n_bins*n_classes] class counts per bin.
  *  gain32_dev  device float [m*n_proj*(n_bins-1)] float gain of every
  *              candidate (-1 where a side is empty), or NULL.
+ *  bounds_dev  device float [m*n_proj*(n_bins-1)] boundaries t_1..t_{B-1}
+ *              of every projection, or NULL.
  * Asynchronous; uses the internal arena. */
 so_status so_histograms(const so_dataset *ds, const int32_t *idx, int64_t n_total,
                         const int64_t *node_off, int32_t m, const so_projs *projs,
-                        int32_t n_bins, float *minmax_dev, int32_t *hist_dev, float *gain32_dev,
-                        void *stream);
+                        const so_split_params *params, float *minmax_dev, int32_t *hist_dev,
+                        float *gain32_dev, float *bounds_dev, void *stream);
 
 /* Tree growth parameters.
- *  n_bins, sort_below, hist_only, rescore_rel_eps  as in so_split_params.
+ *  n_bins, sort_below, hist_only, rescore_rel_eps, bin_rule  as in
+ *             so_split_params; random-width boundaries use the tree's node keys.
  *  n_proj     projections sampled per node, 1..1024.
  *  lambda, nnz_cap  nnz law of a projection: min(nnz_cap, d, 1+Poisson(lambda)).
  *  seed, tree_id    root key = splitmix64(seed ^ tree_id*0x9E3779B97F4A7C15);
@@ -246,6 +271,7 @@ typedef struct {
     uint64_t seed;
     int32_t tree_id;
     int32_t max_depth;
+    int32_t bin_rule;
 } so_tree_params;
 
 /* A trained tree in breadth-first order (children appended level by level in
@@ -317,8 +343,10 @@ so_status so_predict(const float *X, int64_t n, int32_t d, int64_t ld, const so_
  * histogram path is no slower per node (2048 if it never is).  Other fields
  * of params are kept.  Times per size go to times_ms_host [2*n_sizes] when
  * not NULL (exact, histogram), with the sizes in sizes_host [n_sizes];
- * n_sizes_out receives the count (at most 16).  Takes well under a second;
- * synchronises `stream`; uses the internal arena. */
+ * n_sizes_out receives the count (at most 16).  The timed searches use
+ * params->n_bins and params->bin_rule (random width with keys of their own;
+ * params->bin_keys is not read).  Takes well under a second; synchronises
+ * `stream`; uses the internal arena. */
 so_status so_autotune(const so_dataset *ds, int32_t n_proj, double lambda, int32_t nnz_cap,
                       so_split_params *params, int32_t *sizes_host, float *times_ms_host,
                       int32_t *n_sizes_out, void *stream);

@@ -117,11 +117,17 @@ so_status check_dataset(const so_dataset* ds) {
   return SO_OK;
 }
 
-so_status check_params(const so_split_params* p) {
+// keys_given: the caller supplies the random-width node keys through
+// p->bin_keys (the tree trainer and the autotuner use keys of their own).
+so_status check_params(const so_split_params* p, bool keys_given = true) {
   if (!p) return fail(SO_EINVAL, "params is NULL");
   if (p->n_bins < 2 || p->n_bins > kMaxBins) return fail(SO_EINVAL, "n_bins=%d outside 2..256", p->n_bins);
   if (p->sort_below < 0 || p->sort_below > kMaxSortBelow)
     return fail(SO_EINVAL, "sort_below=%d outside 0..%d", p->sort_below, kMaxSortBelow);
+  if (p->bin_rule != SO_BINS_EQUAL_WIDTH && p->bin_rule != SO_BINS_RANDOM_WIDTH)
+    return fail(SO_EINVAL, "bin_rule=%d is neither equal width (0) nor random width (1)", p->bin_rule);
+  if (keys_given && p->bin_rule == SO_BINS_RANDOM_WIDTH && !p->bin_keys)
+    return fail(SO_EINVAL, "random-width bins need bin_keys");
   return SO_OK;
 }
 
@@ -169,11 +175,12 @@ ProjView csr_view(const so_projs* pr) {
   return v;
 }
 
-size_t search_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, int32_t T, int32_t hist_only) {
+size_t search_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, int32_t T, int32_t hist_only,
+                    int32_t bin_rule) {
   Carver cv;
   cv.dry = true;
   SearchScratch s;
-  carve_search(cv, s, m, n_total, P, C, B, T, hist_only);
+  carve_search(cv, s, m, n_total, P, C, B, T, hist_only, bin_rule);
   return cv.used + 256;
 }
 
@@ -185,9 +192,10 @@ size_t batch_vbuf_floats(int32_t m, int64_t n_total, int32_t P) {
   return m > 1 ? (size_t)P * (size_t)n_total : 0;
 }
 
-size_t batch_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, int32_t T, int32_t hist_only) {
+size_t batch_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, int32_t T, int32_t hist_only,
+                   int32_t bin_rule) {
   const size_t vb = batch_vbuf_floats(m, n_total, P);
-  return search_bytes(m, n_total, P, C, B, T, hist_only) + (vb ? vb * sizeof(float) + 256 : 0);
+  return search_bytes(m, n_total, P, C, B, T, hist_only, bin_rule) + (vb ? vb * sizeof(float) + 256 : 0);
 }
 
 template <typename F>
@@ -239,7 +247,8 @@ size_t so_split_search_ws_bytes(int32_t m, int64_t n_total, int32_t n_proj, int3
                                 const so_split_params* params) {
   if (!params || m < 0 || n_proj < 1 || n_classes < 1) return 0;
   const size_t extra = 4096 + sizeof(so_split) + 64 * (size_t)n_classes;
-  return batch_bytes(m, n_total, n_proj, n_classes, params->n_bins, params->sort_below, params->hist_only) + extra;
+  return batch_bytes(m, n_total, n_proj, n_classes, params->n_bins, params->sort_below, params->hist_only,
+                     params->bin_rule) + extra;
 }
 
 so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_t n_total, const int64_t* node_off,
@@ -254,7 +263,8 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     if (n_total < 0 || n_total > INT32_MAX) return fail(SO_EINVAL, "n_total out of range");
     cudaStream_t cs = (cudaStream_t)stream;
     const int C = ds->n_classes, P = projs->n_proj;
-    const size_t need = batch_bytes(m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only);
+    const size_t need =
+        batch_bytes(m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only, params->bin_rule);
     ArenaLease lease;
     char* base = (char*)workspace;
     size_t cap = ws_bytes;
@@ -269,7 +279,7 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     cv.base = base;
     cv.cap = cap;
     SearchScratch s;
-    carve_search(cv, s, m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only);
+    carve_search(cv, s, m, n_total, P, C, params->n_bins, params->sort_below, params->hist_only, params->bin_rule);
     const size_t vbf = batch_vbuf_floats(m, n_total, P);
     float* vbuf = vbf ? cv.take<float>(vbf) : nullptr;
     if (!cv.ok()) return fail(SO_ENOMEM, "workspace too small");
@@ -288,6 +298,8 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     a.max_nnz = projs_max_nnz(projs);
     a.out = out_dev;
     a.left_counts = left_counts_dev;
+    a.bin_rule = params->bin_rule;
+    a.bin_keys = params->bin_keys;
     SO_CK(launch_search(a, s, cs));
     return SO_OK;
   });
@@ -304,7 +316,8 @@ so_status so_split_search(const so_dataset* ds, const int32_t* idx, int64_t n_no
     if (n_node > 0 && !idx) return fail(SO_EINVAL, "idx is NULL");
     cudaStream_t cs = (cudaStream_t)stream;
     const int C = ds->n_classes, P = projs->n_proj;
-    const size_t need = search_bytes(1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only) +
+    const size_t need = search_bytes(1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only,
+                                     params->bin_rule) +
                         4096 + sizeof(so_split) + 64 * C;
     ArenaLease lease;
     char* base = (char*)workspace;
@@ -323,7 +336,7 @@ so_status so_split_search(const so_dataset* ds, const int32_t* idx, int64_t n_no
     so_split* out_dev = cv.take<so_split>(1);
     int64_t* lc = cv.take<int64_t>(kMaxClasses);
     SearchScratch s;
-    carve_search(cv, s, 1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only);
+    carve_search(cv, s, 1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only, params->bin_rule);
     if (!cv.ok()) return fail(SO_ENOMEM, "workspace too small");
     SO_CK(launch_fill_off(off, n_node, cs));
     SearchArgs a;
@@ -340,6 +353,8 @@ so_status so_split_search(const so_dataset* ds, const int32_t* idx, int64_t n_no
     a.max_nnz = projs_max_nnz(projs);
     a.out = out_dev;
     a.left_counts = lc;
+    a.bin_rule = params->bin_rule;
+    a.bin_keys = params->bin_keys;
     SO_CK(launch_search(a, s, cs));
     int64_t lch[kMaxClasses];
     SO_CK(cudaMemcpyAsync(out_host, out_dev, sizeof(so_split), cudaMemcpyDeviceToHost, cs));
@@ -488,12 +503,12 @@ so_status so_sample_projections(int32_t m, const uint64_t* keys, int32_t n_proj,
 }
 
 so_status so_histograms(const so_dataset* ds, const int32_t* idx, int64_t n_total, const int64_t* node_off,
-                        int32_t m, const so_projs* projs, int32_t n_bins, float* minmax_dev, int32_t* hist_dev,
-                        float* gain32_dev, void* stream) {
+                        int32_t m, const so_projs* projs, const so_split_params* params, float* minmax_dev,
+                        int32_t* hist_dev, float* gain32_dev, float* bounds_dev, void* stream) {
   return guarded([&]() -> so_status {
     so_status st;
-    if ((st = check_dataset(ds)) || (st = check_projs(projs))) return st;
-    if (n_bins < 2 || n_bins > kMaxBins) return fail(SO_EINVAL, "n_bins outside 2..256");
+    if ((st = check_dataset(ds)) || (st = check_projs(projs)) || (st = check_params(params))) return st;
+    const int32_t n_bins = params->n_bins, rule = params->bin_rule;
     if (m < 0) return fail(SO_EINVAL, "m < 0");
     if (m == 0) return SO_OK;
     if (!idx || !node_off || !minmax_dev || !hist_dev) return fail(SO_EINVAL, "NULL argument");
@@ -502,7 +517,7 @@ so_status so_histograms(const so_dataset* ds, const int32_t* idx, int64_t n_tota
     Carver dry;
     dry.dry = true;
     SearchScratch ds0;
-    carve_search(dry, ds0, m, n_total, P, C, n_bins, 0, 1);
+    carve_search(dry, ds0, m, n_total, P, C, n_bins, 0, 1, rule);
     dry.take<float>((size_t)m * P * (n_bins - 1));
     ArenaLease lease;
     if ((st = lease.acquire(dry.used + 4096, cs))) return st;
@@ -510,7 +525,7 @@ so_status so_histograms(const so_dataset* ds, const int32_t* idx, int64_t n_tota
     cv.base = (char*)lease.ptr();
     cv.cap = lease.cap();
     SearchScratch s;
-    carve_search(cv, s, m, n_total, P, C, n_bins, 0, 1);
+    carve_search(cv, s, m, n_total, P, C, n_bins, 0, 1, rule);
     float* gtmp = cv.take<float>((size_t)m * P * (n_bins - 1));
     if (!cv.ok()) return fail(SO_ENOMEM, "arena too small");
     SearchArgs a;
@@ -527,6 +542,9 @@ so_status so_histograms(const so_dataset* ds, const int32_t* idx, int64_t n_tota
     a.minmax_out = minmax_dev;
     a.hist_out = hist_dev;
     a.gain32_out = gain32_dev;
+    a.bounds_out = bounds_dev;
+    a.bin_rule = rule;
+    a.bin_keys = params->bin_keys;
     SO_CK(launch_hist_inspect(a, s, gain32_dev ? gtmp : nullptr, cs));
     return SO_OK;
   });
@@ -549,8 +567,8 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
     memset(out, 0, sizeof(*out));
     if (n_root < 1 || n_root > INT32_MAX / 2) return fail(SO_EINVAL, "n_root out of range");
     if (!root_idx) return fail(SO_EINVAL, "root_idx is NULL");
-    so_split_params sp{tp->n_bins, tp->sort_below, tp->hist_only, tp->rescore_rel_eps};
-    if ((st = check_params(&sp))) return st;
+    so_split_params sp{tp->n_bins, tp->sort_below, tp->hist_only, tp->rescore_rel_eps, tp->bin_rule, nullptr};
+    if ((st = check_params(&sp, false))) return st;
     if (tp->n_proj < 1 || tp->n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj outside 1..1024");
     if (tp->nnz_cap < 1 || tp->nnz_cap > kMaxCap) return fail(SO_EINVAL, "nnz_cap outside 1..32");
     if (!(tp->lambda >= 0.0) || !std::isfinite(tp->lambda)) return fail(SO_EINVAL, "lambda must be >= 0");
@@ -615,7 +633,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
       td->cap = cap;
       td->C = C;
       *stats = cv.take<LevelStats>(1);
-      carve_search(cv, *ss, (int32_t)Mb, n_root, P, C, B, T, HO);
+      carve_search(cv, *ss, (int32_t)Mb, n_root, P, C, B, T, HO, tp->bin_rule);
       *vbuf = use_vbuf ? cv.take<float>((size_t)P * (size_t)n_root) : nullptr;
     };
     int32_t *idx_a, *idx_b, *snnz, *sbeg, *send, *sfeat;
@@ -710,6 +728,8 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
           a.out = spl + j0;
           a.left_counts = lc + j0 * C;
           a.vbuf = vbuf;
+          a.bin_rule = tp->bin_rule;
+          a.bin_keys = cur.key + j0;  // random-width boundaries from the node keys
           e = launch_search(a, ss, ls);
           if (e == cudaSuccess)
             e = launch_tree_record_splits((int32_t)j0, mb, cur, spl, snnz, sfeat, ssign, P, cap, td, ls);
@@ -835,7 +855,7 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
                       void* stream) {
   return guarded([&]() -> so_status {
     so_status st;
-    if ((st = check_dataset(ds)) || (st = check_params(params))) return st;
+    if ((st = check_dataset(ds)) || (st = check_params(params, false))) return st;
     if (n_proj < 1 || n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj outside 1..1024");
     if (nnz_cap < 1 || nnz_cap > kMaxCap) return fail(SO_EINVAL, "nnz_cap outside 1..32");
     if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SO_EINVAL, "lambda must be finite and >= 0");
@@ -869,7 +889,7 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
       *sfeat = cv.take<int32_t>((size_t)mcap * P * cap);
       *ssign = cv.take<int8_t>((size_t)mcap * P * cap);
       *out = cv.take<so_split>(mcap);
-      carve_search(cv, *ss, mcap, ncap, P, C, B, kMaxSortBelow, 1);  // histogram scratch for every node
+      carve_search(cv, *ss, mcap, ncap, P, C, B, kMaxSortBelow, 1, params->bin_rule);  // histogram scratch, every node
       *vbuf = cv.take<float>((size_t)P * (size_t)max_nt);
     };
     int32_t *idx, *snnz, *sbeg, *send, *sfeat;
@@ -916,6 +936,8 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
         a.out = out;
         a.left_counts = nullptr;
         a.vbuf = m > 1 ? vbuf : nullptr;
+        a.bin_rule = params->bin_rule;
+        a.bin_keys = keys;
         SO_CK(launch_search(a, ss, cs));  // warm-up
         SO_CK(cudaEventRecord(e0, cs));
         const int reps = 3;

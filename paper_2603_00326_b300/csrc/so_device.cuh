@@ -12,6 +12,7 @@ namespace sof {
 
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;       // splitmix64 increment
 constexpr uint64_t kProjMult = 0xD2B74407B1CE6E93ull;    // separates projection streams
+constexpr uint64_t kBinTag = 0x6A09E667F3BCC908ull;      // frac(sqrt 2): tags the boundary streams
 
 // Order-preserving map float -> uint32 (total order of finite floats, -0 < +0).
 __device__ __forceinline__ uint32_t f2key(float f) {
@@ -115,6 +116,41 @@ __device__ __forceinline__ uint64_t sm64_next(uint64_t& s) {
 __device__ __forceinline__ uint64_t sm64(uint64_t x) {
   uint64_t s = x;
   return sm64_next(s);
+}
+// Output j (0-based) of the generator whose state is s0: the state after j+1
+// increments, mixed.
+__device__ __forceinline__ uint64_t sm64_at(uint64_t s0, int j) {
+  uint64_t s = s0 + (uint64_t)j * kGamma;
+  return sm64_next(s);
+}
+
+// ---- random-width boundaries (the YDF default of the paper's Section 1
+// footnote): projection p of the node with key K draws B-1 splitmix64 outputs
+// from state sm64((K ^ kBinTag) + p*kProjMult); the top 23 bits u of each,
+// sorted, give t = min + ((2u+1) 2^-24) * (max - min), float, two roundings.
+__device__ __forceinline__ uint64_t rw_state(uint64_t key, int p) {
+  return sm64((key ^ kBinTag) + (uint64_t)p * kProjMult);
+}
+__device__ __forceinline__ float rw_boundary(uint32_t u, float mn, float w) {
+  const float f = __fmul_rn(__uint2float_rn(2u * u + 1u), 0x1p-24f);  // exact: 2u+1 < 2^24
+  return __fadd_rn(mn, __fmul_rn(f, w));
+}
+// Guide cell of v: every step (one fused multiply-add, round down to an
+// integer, clamp) is monotone non-decreasing in v, so cell(t) < cell(v)
+// implies t < v and cell(t) > cell(v) implies t > v.  NaN maps to cell 0.
+__device__ __forceinline__ int rw_cell(float v, float s, float o) {
+  const int c = __float2int_rd(__fmaf_rn(v, s, o));
+  return min(max(c, 0), kRwCells - 1);
+}
+// Upper-bound count #{j < nb : t[j] <= v} by binary search (any rule).
+__device__ __forceinline__ int bin_search(const float* __restrict__ t, int nb, float v) {
+  int lo = 0, hi = nb;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(t + mid) <= v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
 }
 
 // ---- warp helpers ---------------------------------------------------------

@@ -10,7 +10,8 @@
 //
 //   k_groups       per histogram node: greedy grouping of its projections
 //   k_mm_staged    per item: min / max of every projection (Section 3 step 2)
-//   k_hist_staged  per item: equal-width bins and class counts in shared
+//   k_hist_staged  per item: bins (equal-width, or random-width from the
+//                  boundary tables of so_rw.cu) and class counts in shared
 //                  memory, flushed with integer atomics (Section 3 step 2)
 //
 // Exact bins without search loops.  With W = (max-min)/B and
@@ -86,8 +87,35 @@ __device__ __forceinline__ unsigned lds_u16(unsigned a) {
   asm volatile("ld.shared.u16 %0, [%1];\n" : "=h"(v) : "r"(a));
   return v;
 }
+__device__ __forceinline__ unsigned lds_u8(unsigned a) {
+  unsigned short v;
+  asm volatile("ld.shared.u8 %0, [%1];\n" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float lds_f32(unsigned a) { return __uint_as_float(lds_u32(a)); }
 __device__ __forceinline__ void reds_add(unsigned a, unsigned v) {
   asm volatile("red.shared.add.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
+}
+
+// Random-width bin #{j < nb : t_j <= v} over a projection's sorted boundaries
+// at shared address tb.  GUIDED: start at the guide's count for v's cell (a
+// lower bound of the bin) and step up while the next boundary is <= v; the
+// guide at gb and the cell map (s, o) come from so_rw.cu.  Otherwise a binary
+// search.  Both loops are bounded by nb.
+template <bool GUIDED>
+__device__ __forceinline__ int rw_bin_smem(float v, float s, float o, unsigned tb, unsigned gb, int nb) {
+  if (GUIDED) {
+    int b = (int)lds_u8(gb + (unsigned)rw_cell(v, s, o));
+    while (b < nb && lds_f32(tb + 4u * (unsigned)b) <= v) ++b;
+    return b;
+  }
+  int lo = 0, hi = nb;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (lds_f32(tb + 4u * (unsigned)mid) <= v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
 }
 
 // ---- packed FP32x2 (sm_100+ PTX) ------------------------------------------
@@ -861,17 +889,38 @@ __device__ __forceinline__ void hist_tile_slow(unsigned tile, unsigned yo_tile, 
     if (yo[i] >= 0) atomicAdd(&s_hist[wbase + bin_of(acc[i], bp.mn, bp.W, bp.inv_w, B) * C + (yo[i] >> 2)], bp.inc);
 }
 
+// Random-width bins of a tile: the packed projection of hist_tile_fast, then
+// per sample the bin from the projection's boundary tables in shared memory
+// (bp.mn, bp.W hold the cell map's s and o; bp.hb the pair's counter base).
+template <int V, int NQ, bool GUIDED>
+__device__ __forceinline__ void hist_tile_rw(unsigned tile, unsigned yo_tile, unsigned dpk, int k, int lane,
+                                             const BinParams& bp, unsigned tb, unsigned gb, int nb, unsigned C4,
+                                             unsigned limit) {
+  float2 acc[V * NQ / 2];
+  int yo[V * NQ];
+  project_tile2<V, NQ>(tile, dpk, k, lane, acc);
+  tile_offsets<V, NQ>(yo_tile, lane, yo);
+#pragma unroll
+  for (int i = 0; i < V * NQ / 2; ++i) {
+    const unsigned bx = (unsigned)rw_bin_smem<GUIDED>(acc[i].x, bp.mn, bp.W, tb, gb, nb);
+    const unsigned by = (unsigned)rw_bin_smem<GUIDED>(acc[i].y, bp.mn, bp.W, tb, gb, nb);
+    reds_add(min(bx * C4 + (bp.hb + (unsigned)yo[2 * i]), limit), bp.inc);
+    reds_add(min(by * C4 + (bp.hb + (unsigned)yo[2 * i + 1]), limit), bp.inc);
+  }
+}
+
 // The item's tile loop for tile width St = 32 * V * NQ.  Three tile buffers,
 // one barrier per tile; labels go through a register one tile ahead.  Warp w
 // evaluates its assigned projections (at most kHistPPW) with their bin
 // parameters in registers.
-template <int V, int NQ>
+template <int V, int NQ, bool RW>
 __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
                                           int U, bool contig, float* s_tile, const uint8_t* s_lab, int* s_yo,
                                           const int* s_rowfeat,
                                           const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk, const uint32_t* s_dpk,
                                           int kmax, const float4* s_bpf, const int4* s_bpi, int B, int HS,
-                                          unsigned C4, unsigned limit, uint32_t* s_hist, int lane, int warp) {
+                                          unsigned C4, unsigned limit, uint32_t* s_hist, unsigned rwt, unsigned rwg,
+                                          int lane, int warp) {
   constexpr int St = 32 * V * NQ;
   const int C = ds.C;
   const int ntile = (int)((it.end - it.beg + St - 1) / St);
@@ -922,11 +971,18 @@ __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* 
 #pragma unroll
     for (int sl = 0; sl < kHistPPW; ++sl) {
       if (pls[sl] >= 0) {
-        if (bps[sl].fast)
-          hist_tile_fast<V, NQ>(tile, lab, su32(s_dpk) + 4u * pls[sl] * kmax, ks[sl], lane, bps[sl], C4, limit_abs);
-        else
-          hist_tile_slow<V, NQ>(tile, lab, su32(s_dpk) + 4u * pls[sl] * kmax, ks[sl], lane, bps[sl], B, C, (pls[sl] >> 1) * HS,
-                              s_hist);
+        const unsigned dpk = su32(s_dpk) + 4u * pls[sl] * kmax;
+        if (RW) {
+          const unsigned tb = rwt + 4u * kRwRow * pls[sl], gb = rwg + kRwRow * pls[sl];
+          if (bps[sl].fast)
+            hist_tile_rw<V, NQ, true>(tile, lab, dpk, ks[sl], lane, bps[sl], tb, gb, B - 1, C4, limit_abs);
+          else
+            hist_tile_rw<V, NQ, false>(tile, lab, dpk, ks[sl], lane, bps[sl], tb, gb, B - 1, C4, limit_abs);
+        } else if (bps[sl].fast) {
+          hist_tile_fast<V, NQ>(tile, lab, dpk, ks[sl], lane, bps[sl], C4, limit_abs);
+        } else {
+          hist_tile_slow<V, NQ>(tile, lab, dpk, ks[sl], lane, bps[sl], B, C, (pls[sl] >> 1) * HS, s_hist);
+        }
       }
     }
   }
@@ -937,11 +993,12 @@ __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* 
 // gathering the feature columns again).  No tiles and no barriers: each warp
 // streams its assigned projections over the item, four samples per lane and
 // four steps in flight.
+template <bool RW>
 __device__ __forceinline__ void hist_item_buf(const float* __restrict__ vbuf, int64_t n_total, const ItemPos& it,
                                               unsigned lab_base, const int* s_assign, int nslot,
                                               const float4* s_bpf, const int4* s_bpi, int B, int C, int HS,
-                                              unsigned C4, unsigned limit_abs, uint32_t* s_hist, int lane,
-                                              int warp) {
+                                              unsigned C4, unsigned limit_abs, uint32_t* s_hist, unsigned rwt,
+                                              unsigned rwg, int lane, int warp) {
   const int len = (int)(it.end - it.beg);
   for (int sl = 0; sl < nslot; ++sl) {
     const int pl = s_assign[warp * nslot + sl];
@@ -964,7 +1021,15 @@ __device__ __forceinline__ void hist_item_buf(const float* __restrict__ vbuf, in
 #pragma unroll
         for (int w = 0; w < 4; ++w) yo[4 * u + w] = label_off8((lw >> (8 * w)) & 0xffu);
       }
-      if (bp.fast) {
+      if (RW) {
+        const unsigned tb = rwt + 4u * kRwRow * pl, gb = rwg + kRwRow * pl;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const unsigned b = (unsigned)(bp.fast ? rw_bin_smem<true>(v[i], bp.mn, bp.W, tb, gb, B - 1)
+                                                : rw_bin_smem<false>(v[i], bp.mn, bp.W, tb, gb, B - 1));
+          reds_add(min(b * C4 + (bp.hb + (unsigned)yo[i]), limit_abs), bp.inc);
+        }
+      } else if (bp.fast) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const float tq = __fadd_rn(__fmaf_rn(v[i], bp.inv_w, bp.c), kMagic);
@@ -984,11 +1049,12 @@ __device__ __forceinline__ void hist_item_buf(const float* __restrict__ vbuf, in
   }
 }
 
-template <int KMAX>
+template <int KMAX, bool RW>
 __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, const int32_t* __restrict__ idx,
                                                               ProjView pv, StagedPlan sp, int B, int PG,
                                                               const uint32_t* __restrict__ mm, int32_t* hist,
-                                                              const float* __restrict__ vbuf, int64_t n_total) {
+                                                              const float* __restrict__ vbuf, int64_t n_total,
+                                                              RwTables rw) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
   const int C = ds.C;
@@ -1000,7 +1066,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   uint8_t* s_lab = reinterpret_cast<uint8_t*>(s_tile + 3 * kTileF);          // [kMaxItem + 512] item labels
   int* s_yo = reinterpret_cast<int*>(s_lab + kMaxItem + 512);                // [3][256] tile label offsets
   uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_yo + 3 * 256);            // [hist_words]
-  uint32_t* s_dpk = s_hist + hist_words;                                     // [kHistPGMax*KMAX]
+  float* s_rwt = reinterpret_cast<float*>(s_hist + hist_words);              // RW: [PG][kRwRow] boundaries
+  uint8_t* s_rwg = reinterpret_cast<uint8_t*>(s_rwt + (RW ? PG * kRwRow : 0));  // RW: [PG][kRwRow] guide
+  uint32_t* s_dpk = reinterpret_cast<uint32_t*>(s_rwg + (RW ? PG * kRwRow : 0));  // [kHistPGMax*KMAX]
   int* s_dk = reinterpret_cast<int*>(s_dpk + kHistPGMax * KMAX);             // [kHistPGMax]
   int* s_assign = s_dk + kHistPGMax;                                         // [kHistPGMax]
   int* s_rowfeat = s_assign + kHistPGMax;                                    // [kStUMax]
@@ -1035,7 +1103,22 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
     } else if (threadIdx.x < it.np) {
       s_dk[threadIdx.x] = 1;  // every projection costs the same when its values are read back
     }
-    if (threadIdx.x < it.np) {
+    if (RW) {
+      // the group's boundary rows and guides, 16 bytes per copy
+      const int64_t row0 = (it.h * P + it.p0) * (int64_t)kRwRow;
+      const int4* gt = reinterpret_cast<const int4*>(rw.t + row0);
+      const int4* gg = reinterpret_cast<const int4*>(rw.g + row0);
+      int4* st4 = reinterpret_cast<int4*>(s_rwt);
+      int4* sg4 = reinterpret_cast<int4*>(s_rwg);
+      for (int e = threadIdx.x; e < it.np * (kRwRow / 4); e += kStThreads) st4[e] = gt[e];
+      for (int e = threadIdx.x; e < it.np * (kRwRow / 16); e += kStThreads) sg4[e] = gg[e];
+      if (threadIdx.x < it.np) {
+        const int pl = threadIdx.x;
+        const float2 so = rw.so[it.h * P + it.p0 + pl];
+        s_bpf[pl] = make_float4(so.x, so.y, 0.0f, 0.0f);
+        s_bpi[pl] = make_int4((pl >> 1) * HS * 4, (int)(1u << (16 * (pl & 1))), so.x >= 0.0f ? 1 : 0, 0);
+      }
+    } else if (threadIdx.x < it.np) {
       const int pl = threadIdx.x;
       const float mn = key2f(mm[(it.h * P + it.p0 + pl) * 2]);
       const float mx = key2f(mm[(it.h * P + it.p0 + pl) * 2 + 1]);
@@ -1064,19 +1147,20 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         }
         s_lab[e] = (uint8_t)b;
       }
+      const unsigned rwt = su32(s_rwt), rwg = su32(s_rwg);
       if (vbuf) {
         __syncthreads();  // labels and warp assignment visible
-        hist_item_buf(vbuf, n_total, it, su32(s_lab), s_assign, nslot, s_bpf, s_bpi, B, C, HS, C4,
-                      su32(s_hist) + limit, s_hist, lane, warp);
+        hist_item_buf<RW>(vbuf, n_total, it, su32(s_lab), s_assign, nslot, s_bpf, s_bpi, B, C, HS, C4,
+                          su32(s_hist) + limit, s_hist, rwt, rwg, lane, warp);
       } else if (St == 256)
-        hist_item<4, 2>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
-                     s_bpi, B, HS, C4, limit, s_hist, lane, warp);
+        hist_item<4, 2, RW>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
+                            s_bpf, s_bpi, B, HS, C4, limit, s_hist, rwt, rwg, lane, warp);
       else if (St == 128)
-        hist_item<4, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
-                     s_bpi, B, HS, C4, limit, s_hist, lane, warp);
+        hist_item<4, 1, RW>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
+                            s_bpf, s_bpi, B, HS, C4, limit, s_hist, rwt, rwg, lane, warp);
       else
-        hist_item<2, 1>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX, s_bpf,
-                     s_bpi, B, HS, C4, limit, s_hist, lane, warp);
+        hist_item<2, 1, RW>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
+                            s_bpf, s_bpi, B, HS, C4, limit, s_hist, rwt, rwg, lane, warp);
     } else {
       // direct path for wide groups (rare): one warp per projection, gathers
       for (int pl = warp; pl < it.np; pl += kStWarps) {
@@ -1096,7 +1180,15 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
             acc = __fadd_rn(acc, pv.sign[rb + jj] == 1 ? x : -x);
           }
           const int yv = ds.y[s];
-          if (yv < C) atomicAdd(&s_hist[(pl >> 1) * HS + bin_of(acc, bf.x, bf.y, bf.z, B) * C + yv], inc);
+          int b;
+          if (RW) {
+            const unsigned tb = su32(s_rwt) + 4u * kRwRow * pl, gb = su32(s_rwg) + kRwRow * pl;
+            b = bf.x >= 0.0f ? rw_bin_smem<true>(acc, bf.x, bf.y, tb, gb, B - 1)
+                             : rw_bin_smem<false>(acc, bf.x, bf.y, tb, gb, B - 1);
+          } else {
+            b = bin_of(acc, bf.x, bf.y, bf.z, B);
+          }
+          if (yv < C) atomicAdd(&s_hist[(pl >> 1) * HS + b * C + yv], inc);
         }
       }
     }
@@ -1117,9 +1209,10 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
 }
 
 // ---- host side ----------------------------------------------------------------
-int hist_group_size(int B, int C) {
-  // 16-bit counters, two projections per word, in <= 100 KB of shared memory
-  const int pair_bytes = (B + 1) * C * 4;
+int hist_group_size(int B, int C, bool rw) {
+  // 16-bit counters, two projections per word, plus the random-width tables
+  // (boundaries and guide of each projection), in <= 100 KB of shared memory
+  const int pair_bytes = (B + 1) * C * 4 + (rw ? 2 * kRwRow * 5 : 0);
   int pg = 2 * ((100 * 1024) / pair_bytes);
   return pg < 1 ? 1 : (pg > kHistPGMax ? kHistPGMax : pg);
 }
@@ -1131,11 +1224,12 @@ size_t mm_smem_bytes(int /*d*/, int kmax) {
   return (size_t)3 * kTileF * 4 + (size_t)kMmGroup * 32 * 8 + (size_t)kMmGroup * kmax * 4 + kMmGroup * 8 +
          kStUMax * 12;
 }
-size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG) {
+size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG, bool rw) {
   const int npair = (PG + 1) >> 1;
   const size_t hist_words = ((size_t)npair * (B + 1) * C + 1 + 3) & ~(size_t)3;
-  return (size_t)3 * kTileF * 4 + kMaxItem + 512 + 3 * 256 * 4 + hist_words * 4 + (size_t)kHistPGMax * kmax * 4 +
-         kHistPGMax * 8 + kStUMax * 12;
+  const size_t rw_bytes = rw ? (size_t)PG * kRwRow * 5 : 0;
+  return (size_t)3 * kTileF * 4 + kMaxItem + 512 + 3 * 256 * 4 + hist_words * 4 + rw_bytes +
+         (size_t)kHistPGMax * kmax * 4 + kHistPGMax * 8 + kStUMax * 12;
 }
 
 bool staged_supported(int d) { return d <= kStMaxWords * 32; }
@@ -1153,10 +1247,12 @@ void carve_staged(Carver& cv, StagedScratch& s, int64_t m_hist_cap, int P) {
 
 template <int KMAX>
 cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes, int64_t m_hist_cap,
-                            const StagedScratch& ss, uint32_t* mm, int32_t* hist, int64_t S, cudaStream_t st) {
+                            const StagedScratch& ss, uint32_t* mm, int32_t* hist, const RwTables& rw, int64_t S,
+                            cudaStream_t st) {
   const DeviceInfo& di = device_info();
-  const int P = a.pv.P, C = a.ds.C, B = a.B, d = a.ds.d;
-  const int PG = hist_group_size(B, C);
+  const int C = a.ds.C, B = a.B, d = a.ds.d;
+  const bool RW = a.bin_rule == SO_BINS_RANDOM_WIDTH;
+  const int PG = hist_group_size(B, C, RW);
   // histogram items: at most kMaxItem samples (label bytes in shared memory,
   // 16-bit counters); min / max items a quarter of that, so that a single
   // large node still spreads over every SM
@@ -1185,23 +1281,27 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
     ProfScope ps_("k_minmax", st);
     k_mm_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp1, mm, a.vbuf, a.n_total);
   }
+  if (RW) {
+    e = launch_rw_bounds(a, plan_total, hist_nodes, mm, rw, st);
+    if (e != cudaSuccess) return e;
+  }
   {
-    const size_t smem = hist_smem_bytes(d, KMAX, B, C, PG);
-    e = cudaFuncSetAttribute(k_hist_staged<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = hist_smem_bytes(d, KMAX, B, C, PG, RW);
+    auto kern = RW ? k_hist_staged<KMAX, true> : k_hist_staged<KMAX, false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ProfScope ps_("k_hist", st);
-    k_hist_staged<KMAX><<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp2, B, PG, mm, hist, a.vbuf,
-                                                              a.n_total);
+    kern<<<di.num_sms, kStThreads, smem, st>>>(a.ds, a.idx, a.pv, sp2, B, PG, mm, hist, a.vbuf, a.n_total, rw);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_staged(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes, int64_t m_hist_cap,
-                          const StagedScratch& ss, uint32_t* mm, int32_t* hist, int64_t S, int kmax,
-                          cudaStream_t st) {
-  if (kmax <= 8) return launch_staged_k<8>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, S, st);
-  if (kmax <= 16) return launch_staged_k<16>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, S, st);
-  return launch_staged_k<32>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, S, st);
+                          const StagedScratch& ss, uint32_t* mm, int32_t* hist, const RwTables& rw, int64_t S,
+                          int kmax, cudaStream_t st) {
+  if (kmax <= 8) return launch_staged_k<8>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, rw, S, st);
+  if (kmax <= 16) return launch_staged_k<16>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, rw, S, st);
+  return launch_staged_k<32>(a, plan_total, hist_nodes, m_hist_cap, ss, mm, hist, rw, S, st);
 }
 
 }  // namespace sof

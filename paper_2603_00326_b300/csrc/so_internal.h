@@ -16,6 +16,8 @@ constexpr int kMaxCap = 32;        // non-zeros per projection row
 constexpr int kMaxProj = 1024;     // projections per node
 constexpr int kMaxSortBelow = 2048;  // largest exact-path node + 1
 constexpr int kSortRegMax = 128;     // exact-path nodes sorted by one warp in registers
+constexpr int kRwRow = 256;          // random-width table row: B-1 boundaries (padded) or guide cells
+constexpr int kRwCells = 256;        // guide cells per projection
 
 // 4-lane int64 vector carried through the generic device scans.
 struct V4 {
@@ -67,6 +69,19 @@ struct HistTuning {
   int32_t pgroup = 8;     // projections per work item (one warp each)
 };
 
+// Random-width boundary tables of the histogram nodes (one row of kRwRow per
+// histogram slot h and projection p, row h*P + p):
+//  t   boundaries t_1..t_{B-1}, ascending, padded with +inf;
+//  g   guide: g[c] = number of boundaries whose cell is below c (cells of the
+//      monotone map v -> clamp(floor(fma(v, s, o)), 0, kRwCells-1));
+//  so  (s, o) of that map; s < 0 marks a projection without a guide (zero or
+//      ill-conditioned range), binned by binary search.
+struct RwTables {
+  float* t = nullptr;
+  uint8_t* g = nullptr;
+  float2* so = nullptr;
+};
+
 // Everything one batched split search needs.
 struct SearchArgs {
   DatasetView ds;
@@ -86,7 +101,11 @@ struct SearchArgs {
   float* minmax_out = nullptr;
   int32_t* hist_out = nullptr;
   float* gain32_out = nullptr;
+  float* bounds_out = nullptr;      // [m*P*(B-1)] boundaries (so_histograms)
   HistTuning tune{};
+  // SO_BINS_EQUAL_WIDTH or SO_BINS_RANDOM_WIDTH; node keys of the random rule
+  int32_t bin_rule = 0;
+  const uint64_t* bin_keys = nullptr;  // device [m]
   // optional [P][n_total] buffer: the min / max pass stores every
   // histogram-path sample's projected values and the histogram pass reads
   // them back instead of gathering the feature columns again
@@ -121,11 +140,17 @@ struct SearchScratch {
   int32_t* node_cls = nullptr;  // [m*8] class counts of exact-path nodes
   int64_t m_hist_cap = 0;
   StagedScratch staged;
+  RwTables rw;                  // random-width rule only
 };
 
 // Carves a SearchScratch (dry run gives the size).
 void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int32_t P, int32_t C,
-                  int32_t B, int32_t T, int32_t hist_only);
+                  int32_t B, int32_t T, int32_t hist_only, int32_t bin_rule = 0);
+
+// Random-width boundaries, guide and cell map of every (histogram node,
+// projection), from the node keys and the min / max keys mm.
+cudaError_t launch_rw_bounds(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes,
+                             const uint32_t* mm, const RwTables& rw, cudaStream_t st);
 
 // Whether per-stage tracing is on (so_profile_enable).
 bool profiling_on();
@@ -164,7 +189,7 @@ bool staged_supported(int d);
 void carve_staged(Carver& cv, StagedScratch& s, int64_t m_hist_cap, int P);
 cudaError_t launch_staged(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes,
                           int64_t m_hist_cap, const StagedScratch& ss, uint32_t* mm, int32_t* hist,
-                          int64_t S, int kmax, cudaStream_t st);
+                          const RwTables& rw, int64_t S, int kmax, cudaStream_t st);
 
 // ---- partition ------------------------------------------------------------
 // Per-node instruction for the batched stable partition.

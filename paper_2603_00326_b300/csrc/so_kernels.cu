@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(PG * 32) k_hist(DatasetView ds, const int32_t*
                                                  const int64_t* __restrict__ off, ProjView pv,
                                                  const V4* plan_total, const int32_t* hist_nodes,
                                                  const int64_t* item_off, int64_t S, int B,
-                                                 const uint32_t* __restrict__ mm, int32_t* hist) {
+                                                 const uint32_t* __restrict__ mm, int32_t* hist,
+                                                 const float* __restrict__ rw_t) {
   extern __shared__ int32_t s_hist[];  // [PG][B*C]
   __shared__ int32_t s_f[PG][kMaxCap];
   __shared__ int8_t s_s[PG][kMaxCap];
@@ -267,7 +268,8 @@ __global__ void __launch_bounds__(PG * 32) k_hist(DatasetView ds, const int32_t*
         const int64_t s = safe_sample(idx[e], ds.n);
         const int yv = ds.y[s];
         const float v = project_value(ds.X, ds.ld, s, s_f[warp], s_s[warp], k);
-        const int b = bin_of(v, mn, w, inv_w, B);
+        // random width: binary search of the projection's sorted boundaries
+        const int b = rw_t ? bin_search(rw_t + (h * P + p) * kRwRow, B - 1, v) : bin_of(v, mn, w, inv_w, B);
         if (yv < C) atomicAdd(&hp[b * C + yv], 1);  // labels >= C are not counted
       }
     }
@@ -365,7 +367,8 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
                                                      const int64_t* off, int32_t P, int32_t B, int32_t C,
                                                      const int32_t* __restrict__ hist,
                                                      const float* __restrict__ max32,
-                                                     const uint32_t* __restrict__ mm, float eps,
+                                                     const uint32_t* __restrict__ mm,
+                                                     const float* __restrict__ rw_t, float eps,
                                                      so_split* out, int64_t* left_counts) {
   __shared__ float s_red[8];
   __shared__ Cand s_best[8];
@@ -447,7 +450,8 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
       r.proj = f.proj;
       r.path = 0;
       r.cand = f.cand;
-      r.threshold = boundary(mn, w, f.cand + 1);
+      // candidate b's threshold is boundary t_{b+1}
+      r.threshold = rw_t ? rw_t[(h * P + f.proj) * kRwRow + f.cand] : boundary(mn, w, f.cand + 1);
       r.gain = f.g;
       r.n_left = nL;
       r.n_right = n - nL;
@@ -462,7 +466,8 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
 // Copies inspection outputs of the histogram stage (slot h -> node j).
 __global__ void k_hist_export(const V4* plan_total, const int32_t* hist_nodes, int32_t P, int32_t BC,
                               int32_t B, const uint32_t* mm, const int32_t* hist, const float* gain_tmp,
-                              float* minmax_out, int32_t* hist_out, float* gain32_out) {
+                              const float* rw_t, float* minmax_out, int32_t* hist_out, float* gain32_out,
+                              float* bounds_out) {
   const int64_t mh = plan_total->x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -484,13 +489,27 @@ __global__ void k_hist_export(const V4* plan_total, const int32_t* hist_nodes, i
       gain32_out[((int64_t)hist_nodes[h] * P + p) * (B - 1) + r] = gain_tmp[i];
     }
   }
+  if (bounds_out) {
+    for (int64_t i = tid; i < mh * P * (B - 1); i += stride) {
+      const int64_t hp = i / (B - 1), r = i - hp * (B - 1);
+      const int64_t h = hp / P, p = hp - h * P;
+      float t;
+      if (rw_t) {
+        t = rw_t[hp * kRwRow + r];
+      } else {
+        const float mn = key2f(mm[hp * 2]), mx = key2f(mm[hp * 2 + 1]);
+        t = boundary(mn, bin_width(mn, mx, B), (int)r + 1);
+      }
+      bounds_out[((int64_t)hist_nodes[h] * P + p) * (B - 1) + r] = t;
+    }
+  }
 }
 
 // ============================================================================
 // Search driver
 // ============================================================================
 void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int32_t P, int32_t C,
-                  int32_t B, int32_t T, int32_t hist_only) {
+                  int32_t B, int32_t T, int32_t hist_only, int32_t bin_rule) {
   int64_t mh = m;
   if (!hist_only) {
     const int64_t tt = T > 2 ? T : 2;
@@ -511,6 +530,13 @@ void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int3
   s.node_counts = cv.take<int32_t>((size_t)mh * C);
   s.hist = cv.take<int32_t>((size_t)mh * P * B * C);
   carve_staged(cv, s.staged, mh, P);
+  if (bin_rule == SO_BINS_RANDOM_WIDTH) {
+    s.rw.t = cv.take<float>((size_t)mh * P * kRwRow);
+    s.rw.g = cv.take<uint8_t>((size_t)mh * P * kRwRow);
+    s.rw.so = cv.take<float2>((size_t)mh * P);
+  } else {
+    s.rw = RwTables{};
+  }
 }
 
 namespace {
@@ -562,8 +588,10 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
     ProfScope ps_("k_hist_init", st);
     k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
   }
+  const bool rw = a.bin_rule == SO_BINS_RANDOM_WIDTH;
   if (staged_supported(a.ds.d)) {
-    e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, S, a.max_nnz, st);
+    e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, s.rw, S,
+                      a.max_nnz, st);
     if (e != cudaSuccess) return e;
   } else {
     {
@@ -573,6 +601,10 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
       k_minmax<PG><<<di.num_sms * occ_mm, PG * 32, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
                                                             s.hist_nodes, s.item_off, S, s.mm_keys);
     }
+    if (rw) {
+      e = launch_rw_bounds(a, s.plan_total, s.hist_nodes, s.mm_keys, s.rw, st);
+      if (e != cudaSuccess) return e;
+    }
     {
       const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
       e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -580,7 +612,8 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
       const int occ = occupancy(k_hist<PG>, PG * 32, smem);
       ProfScope ps_("k_hist", st);
       k_hist<PG><<<di.num_sms * occ, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
-                                                          s.hist_nodes, s.item_off, S, B, s.mm_keys, s.hist);
+                                                          s.hist_nodes, s.item_off, S, B, s.mm_keys, s.hist,
+                                                          rw ? s.rw.t : nullptr);
     }
   }
   {
@@ -590,7 +623,7 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
   {
     ProfScope ps_("k_hist_select", st);
     k_hist_select<<<grid_fill, 256, 0, st>>>(s.plan_total, s.hist_nodes, a.node_off, P, B, C, s.hist, s.max32,
-                                             s.mm_keys, a.eps, a.out, a.left_counts);
+                                             s.mm_keys, rw ? s.rw.t : nullptr, a.eps, a.out, a.left_counts);
   }
   // exact path
   e = launch_sort_warp(a, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls, st);
@@ -632,8 +665,10 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
     ProfScope ps_("k_hist_init", st);
     k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
   }
+  const bool rw = a.bin_rule == SO_BINS_RANDOM_WIDTH;
   if (staged_supported(a.ds.d)) {
-    e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, S, a.max_nnz, st);
+    e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, s.rw, S,
+                      a.max_nnz, st);
     if (e != cudaSuccess) return e;
   } else {
     {
@@ -641,13 +676,17 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
       k_minmax<PG><<<di.num_sms * 4, PG * 32, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.hist_nodes,
                                                        s.item_off, S, s.mm_keys);
     }
+    if (rw) {
+      e = launch_rw_bounds(a, s.plan_total, s.hist_nodes, s.mm_keys, s.rw, st);
+      if (e != cudaSuccess) return e;
+    }
     const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
     e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     {
       ProfScope ps_("k_hist", st);
       k_hist<PG><<<di.num_sms * 2, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total, s.hist_nodes,
-                                                        s.item_off, S, B, s.mm_keys, s.hist);
+                                                        s.item_off, S, B, s.mm_keys, s.hist, rw ? s.rw.t : nullptr);
     }
   }
   {
@@ -657,7 +696,8 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
   {
     ProfScope ps_("k_hist_export", st);
     k_hist_export<<<grid_fill, 256, 0, st>>>(s.plan_total, s.hist_nodes, P, B * C, B, s.mm_keys, s.hist, gain_tmp,
-                                             a.minmax_out, a.hist_out, a.gain32_out);
+                                             rw ? s.rw.t : nullptr, a.minmax_out, a.hist_out, a.gain32_out,
+                                             a.bounds_out);
   }
   return cudaGetLastError();
 }

@@ -44,7 +44,9 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
       ds->n_classes < 1 || ds->n_classes > kMaxClasses)
     return noalloc_fail(SO_EINVAL, "so_split_search_noalloc: bad dataset");
   if (!params || params->n_bins < 2 || params->n_bins > kMaxBins || params->sort_below < 0 ||
-      params->sort_below > kMaxSortBelow)
+      params->sort_below > kMaxSortBelow ||
+      (params->bin_rule != SO_BINS_EQUAL_WIDTH && params->bin_rule != SO_BINS_RANDOM_WIDTH) ||
+      (params->bin_rule == SO_BINS_RANDOM_WIDTH && !params->bin_keys))
     return noalloc_fail(SO_EINVAL, "so_split_search_noalloc: bad split parameters");
   if (!projs || projs->n_proj < 1 || projs->n_proj > kMaxProj || !projs->ptr || !projs->feat || !projs->sign ||
       projs->max_nnz < 0 || projs->max_nnz > kMaxCap)
@@ -61,7 +63,7 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   dry.take<so_split>(1);
   dry.take<int64_t>(kMaxClasses);
   SearchScratch s0;
-  carve_search(dry, s0, 1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only);
+  carve_search(dry, s0, 1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only, params->bin_rule);
   if (dry.used > kNoallocScratchBytes) {
     snprintf(msg, sizeof(msg),
              "so_split_search_noalloc: this node needs %zu bytes of scratch, above the %zu-byte static "
@@ -97,7 +99,7 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   so_split* out_dev = cv.take<so_split>(1);
   int64_t* lc = cv.take<int64_t>(kMaxClasses);
   SearchScratch s;
-  carve_search(cv, s, 1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only);
+  carve_search(cv, s, 1, n_node, P, C, params->n_bins, params->sort_below, params->hist_only, params->bin_rule);
   if (!cv.ok()) return noalloc_fail(SO_EINTERNAL, "so_split_search_noalloc: scratch layout overflow");
 
   SearchArgs a;
@@ -129,6 +131,8 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   a.max_nnz = (projs->max_nnz >= 1) ? projs->max_nnz : kMaxCap;
   a.out = out_dev;
   a.left_counts = lc;
+  a.bin_rule = params->bin_rule;
+  a.bin_keys = params->bin_keys;
 
   cudaError_t e = launch_fill_off(off, n_node, cs);
   if (e == cudaSuccess) e = launch_search(a, s, cs);

@@ -36,9 +36,13 @@ class so_projs(C.Structure):
                 ("max_nnz", C.c_int32)]
 
 
+SO_BINS_EQUAL_WIDTH = 0
+SO_BINS_RANDOM_WIDTH = 1
+
+
 class so_split_params(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("sort_below", C.c_int32), ("hist_only", C.c_int32),
-                ("rescore_rel_eps", C.c_float)]
+                ("rescore_rel_eps", C.c_float), ("bin_rule", C.c_int32), ("bin_keys", C.c_void_p)]
 
 
 class so_split(C.Structure):
@@ -51,7 +55,7 @@ class so_tree_params(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("sort_below", C.c_int32), ("hist_only", C.c_int32),
                 ("rescore_rel_eps", C.c_float), ("n_proj", C.c_int32), ("lambda_", C.c_double),
                 ("nnz_cap", C.c_int32), ("seed", C.c_uint64), ("tree_id", C.c_int32),
-                ("max_depth", C.c_int32)]
+                ("max_depth", C.c_int32), ("bin_rule", C.c_int32)]
 
 
 class so_tree(C.Structure):
@@ -97,8 +101,8 @@ _SIGS = {
     "so_partition_batch": (_I32, [C.POINTER(so_dataset), _V, _V, _I64, _V, _I32, C.POINTER(so_projs),
                                   _V, _V]),
     "so_sample_projections": (_I32, [_I32, _V, _I32, _I32, _D, _I32, _V, _V, _V, _V]),
-    "so_histograms": (_I32, [C.POINTER(so_dataset), _V, _I64, _V, _I32, C.POINTER(so_projs), _I32,
-                             _V, _V, _V, _V]),
+    "so_histograms": (_I32, [C.POINTER(so_dataset), _V, _I64, _V, _I32, C.POINTER(so_projs),
+                             C.POINTER(so_split_params), _V, _V, _V, _V, _V]),
     "so_train_tree": (_I32, [C.POINTER(so_dataset), _V, _I64, C.POINTER(so_tree_params),
                              C.POINTER(so_tree), _V]),
     "so_tree_free": (None, [C.POINTER(so_tree)]),
@@ -193,8 +197,13 @@ class DeviceProjs:
                         self.max_nnz)
 
 
-def split_params(n_bins=256, sort_below=1024, hist_only=False, rescore_rel_eps=0.0) -> so_split_params:
-    return so_split_params(n_bins, sort_below, 1 if hist_only else 0, rescore_rel_eps)
+def split_params(n_bins=256, sort_below=1024, hist_only=False, rescore_rel_eps=0.0, bin_rule=0,
+                 bin_keys=None) -> so_split_params:
+    """bin_rule SO_BINS_RANDOM_WIDTH needs bin_keys: a device int64 tensor [m]
+    holding the nodes' uint64 keys (kept alive by the returned struct)."""
+    p = so_split_params(n_bins, sort_below, 1 if hist_only else 0, rescore_rel_eps, bin_rule, _ptr(bin_keys))
+    p._keys = bin_keys
+    return p
 
 
 def so_version() -> str:
@@ -308,8 +317,9 @@ def so_sample_projections(keys, n_proj: int, d: int, lam: float, cap: int, strea
 
 
 def so_histograms(ds: DeviceDataset, idx, node_off, projs: DeviceProjs, n_bins: int, want_gains=False,
-                  stream=None):
-    """Histogram stage of m nodes.  Returns (minmax [m,P,2], hist [m,P,B,C], gains [m,P,B-1] or None)."""
+                  stream=None, bin_rule=0, bin_keys=None, want_bounds=False):
+    """Histogram stage of m nodes.  Returns (minmax [m,P,2], hist [m,P,B,C],
+    gains [m,P,B-1] or None); with want_bounds also the boundaries [m,P,B-1]."""
     import torch
     m = int(node_off.numel()) - 1
     P, Cc = projs.n_proj, ds.n_classes
@@ -317,10 +327,14 @@ def so_histograms(ds: DeviceDataset, idx, node_off, projs: DeviceProjs, n_bins: 
     mm = torch.zeros((m, P, 2), dtype=torch.float32, device=dev)
     hist = torch.zeros((m, P, n_bins, Cc), dtype=torch.int32, device=dev)
     gains = torch.zeros((m, P, n_bins - 1), dtype=torch.float32, device=dev) if want_gains else None
+    bounds = torch.zeros((m, P, n_bins - 1), dtype=torch.float32, device=dev) if want_bounds else None
     d = ds.c()
     p = projs.c()
+    prm = split_params(n_bins, bin_rule=bin_rule, bin_keys=bin_keys)
     _check(lib().so_histograms(C.byref(d), _ptr(idx), int(idx.numel()), _ptr(node_off), m, C.byref(p),
-                               n_bins, _ptr(mm), _ptr(hist), _ptr(gains), _stream(stream)))
+                               C.byref(prm), _ptr(mm), _ptr(hist), _ptr(gains), _ptr(bounds), _stream(stream)))
+    if want_bounds:
+        return mm, hist, gains, bounds
     return mm, hist, gains
 
 
@@ -346,9 +360,9 @@ class Tree:
 
 
 def tree_params(n_proj, lam, cap, n_bins=256, sort_below=1024, hist_only=False, seed=0, tree_id=0,
-                max_depth=-1, rescore_rel_eps=0.0) -> so_tree_params:
+                max_depth=-1, rescore_rel_eps=0.0, bin_rule=0) -> so_tree_params:
     return so_tree_params(n_bins, sort_below, 1 if hist_only else 0, rescore_rel_eps, n_proj, lam, cap,
-                          seed & 0xFFFFFFFFFFFFFFFF, tree_id, max_depth)
+                          seed & 0xFFFFFFFFFFFFFFFF, tree_id, max_depth, bin_rule)
 
 
 def so_train_tree(ds: DeviceDataset, root_idx, params: so_tree_params, stream=None) -> Tree:
