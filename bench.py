@@ -134,7 +134,7 @@ def cpu_baseline(ds, pr, n_sample_proj: int, threads: int = 1):
     return ds.n * n_sample_proj / dt, dt
 
 
-def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
+def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=True):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
     64 projections/node, crossover T autotuned), one tree grown to purity
@@ -142,7 +142,7 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
     from paper_2603_00326_b300 import datagen as G
     out = {}
     if only not in (None, "frontier"):
-        return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees)
+        return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees, rw_tree=rw_tree)
     ds_np = G.frontier_1m()
     p = G.WORKLOAD_PARAMS["frontier_1m"]
     idx_np, off_np = G.frontier_nodes(ds_np.n, p["n_nodes"])
@@ -205,10 +205,10 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1):
     del dd, idx, off, ws, outb, views
     if only == "frontier":
         return out
-    return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees)
+    return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees, rw_tree=rw_tree)
 
 
-def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_trees=1):
+def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_trees=1, rw_tree=True):
     from paper_2603_00326_b300 import datagen as G
     if only in (None, "tree"):
         # one tree to purity
@@ -260,6 +260,20 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
                             "max_depth": int(max(int(t.depth.max()) for t in trees)),
                             "predict_sample_trees_per_s": fs.n * forest_trees / pred_s,
                             "oob_accuracy_per_tree": oob_acc}
+        if rw_tree:
+            # tree 0 again with random-width bins (the YDF default of the
+            # paper's Section 1 footnote): time and out-of-bag accuracy
+            import dataclasses
+            rcfg = dataclasses.replace(cfg, n_trees=1, bin_rule=S.SO_BINS_RANDOM_WIDTH)
+            torch.cuda.synchronize()
+            rtrees, rsecs = F.train_forest(rcfg, dd)
+            inbag = np.zeros(fs.n, bool)
+            inbag[F.root_indices(fs.n, 0, rcfg)] = True
+            p1, _ = S.so_predict(dd.X, S.upload_forest(rtrees, 2))
+            out["forest_2m"]["random_width_tree0"] = {
+                "train_s": rsecs, "nodes": rtrees[0].n_nodes, "depth": int(rtrees[0].depth.max()),
+                "oob_accuracy": float((p1.cpu().numpy()[~inbag] == fs.y[~inbag]).mean())}
+            del rtrees
         del dd, trees, fo
     if wide_trees > 0 and only in (None, "wide"):
         # wide count-like data: n=500k, d=4096, 90% zeros, 5 classes, grown to purity
@@ -302,17 +316,87 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
     return out
 
 
+def random_width_step(S, torch, ds, pj, idx, off, n, P, C, n_bins, steps, key):
+    """The root step (search + partition) with random-width bins (the YDF
+    default of the paper's Section 1 footnote) on resident inputs: CUDA-event
+    time per step and per-stage times, with the histogram kernel's roofline."""
+    dev = idx.device
+    keys = torch.tensor([key], dtype=torch.int64, device=dev)
+    prm = S.split_params(n_bins, 0, True, bin_rule=S.SO_BINS_RANDOM_WIDTH, bin_keys=keys)
+    ws = torch.empty(S.so_split_search_ws_bytes(1, n, P, C, prm), dtype=torch.uint8, device=dev)
+    out = torch.empty(S.SPLIT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    lc = torch.empty(C, dtype=torch.int64, device=dev)
+    idx_out = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        S.so_split_search_batch(ds, idx, off, pj, prm, out=out, left_counts=lc, workspace=ws)
+        S.so_partition_batch(ds, idx, idx_out, off, pj, out)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    S.so_profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    S.so_profile_enable(False)
+    prof = S.so_profile_read()
+    ms = ev0.elapsed_time(ev1) / steps
+    stage_ms = {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.items()}
+    rec = S.splits_to_numpy(out)[0]
+    return {"ms_per_step": ms, "sample_projections_per_s": n * P / (ms / 1000.0), "stage_ms_per_launch": stage_ms,
+            "split": {"proj": int(rec["proj"]), "cand": int(rec["cand"]), "gain": float(rec["gain"])}}
+
+
 def run_leg(args):
-    """One secondary leg alone (for profiling): frontier | tree | forest."""
+    """One secondary leg alone (for profiling): frontier | tree | forest | wide | trunk | rw."""
     import torch
     from paper_2603_00326_b300 import soforest as S
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     S.lib()
+    if args.leg == "rw":
+        ds_np, pr, p = make_inputs()
+        n, P, C = ds_np.n, p["n_proj"], ds_np.n_classes
+        ds = S.DeviceDataset(torch.from_numpy(ds_np.X).to(dev), torch.from_numpy(ds_np.y).to(dev), C)
+        pj = S.DeviceProjs(P, torch.from_numpy(pr.ptr).to(dev), torch.from_numpy(pr.feat).to(dev),
+                           torch.from_numpy(pr.sign).to(dev), int(np.diff(pr.ptr).max()))
+        idx = torch.arange(n, dtype=torch.int32, device=dev)
+        off = torch.tensor([0, n], dtype=torch.int64, device=dev)
+        res = random_width_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, rw_key())
+        res.update(_rw_roofline(pr, n, res["stage_ms_per_launch"].get("k_hist")))
+        del ds, pj, idx
+        out = {"root_4m_random_width": res}
+        if args.forest_trees > 0:
+            out.update(extra_legs(S, torch, dev, 1, only="forest", rw_tree=True))
+        print(json.dumps({"leg": args.leg, **out}), flush=True)
+        return 0
     out = extra_legs(S, torch, dev, args.forest_trees if args.leg == "forest" else 0, only=args.leg,
                      wide_trees=args.wide_trees if args.leg == "wide" else 0)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
     return 0
+
+
+def rw_key() -> int:
+    """Node key of the root in the random-width measurements (the full-size
+    parity test uses the same key)."""
+    from paper_2603_00326_b300 import datagen as G
+    return G.PROJ_SEED_BASE + 11
+
+
+def _rw_roofline(pr, n, k_hist_ms):
+    hbm, peak_kind = peaks()
+    alg_bytes = np.unique(pr.feat).size * n * 4 + n * 4 + n * 1
+    if not k_hist_ms:
+        return {}
+    ach = alg_bytes / (k_hist_ms / 1000.0) / 1e9
+    return {"roofline": {"bound": "hbm", "kernel": "k_hist (random width)", "achieved": ach, "peak": hbm,
+                         "unit": "GB/s", "frac": ach / hbm, "peak_source": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": k_hist_ms}}
 
 
 def run_reference(args):
@@ -480,6 +564,10 @@ def run_ours(args):
                   "n_left": int(rec["n_left"])},
     }
     if rank == 0 and world == 1 and not args.no_extras:
+        # the same step with random-width bins, on the resident inputs
+        rw = random_width_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, rw_key())
+        rw.update(_rw_roofline(pr, n, rw["stage_ms_per_launch"].get("k_hist")))
+        line["random_width"] = rw
         line["extras"] = extra_legs(S, torch, dev, args.forest_trees, wide_trees=args.wide_trees)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
@@ -506,7 +594,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the frontier, tree and forest legs")
-    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest", "wide", "trunk"],
+    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest", "wide", "trunk", "rw"],
                     help="run one secondary leg alone and print its JSON")
     ap.add_argument("--forest-trees", type=int, default=2,
                     help="trees of the n=2M, d=256 forest timed in the extras (0 skips)")

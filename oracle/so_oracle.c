@@ -20,9 +20,8 @@
  *   - Step 2, histogram: bin the projected feature and count class instances
  *     per bin (Section 3 step 2; Section 3.2, equal-width 256-bin variant).
  *   - Step 3, split criterion at every bin boundary, best over projections
- *     (Section 3 step 3; Section 3.3 kernel 2).  The criterion is Gini
- *     impurity decrease (the paper's YDF uses entropy; Gini is the chosen
- *     criterion here).
+ *     (Section 3 step 3; Section 3.3 kernel 2).  Two criteria: Gini impurity
+ *     decrease, and entropy (information gain), which the paper's YDF uses.
  *   - Small nodes use an exact split by sorting instead of a histogram, the
  *     switch being node cardinality (Section 3.1, Dynamic Histogramming).
  *   - Trees are grown to purity (Section 2, Background, item 2).
@@ -54,6 +53,16 @@
  *      f_j = (2 u_j + 1) * 2^-24, exact in float and inside (0, 1);
  *      t_j = min + f_j * (max - min), float, two roundings.  Bin, candidates
  *      and thresholds then follow R2 with these t_j.
+ *   R15 entropy criterion: information gain in nats, IG = (f(n) - sum_c f(N_c)
+ *      + sum_c f(L_c) - f(nL) + sum_c f(R_c) - f(nR)) / n with f(x) = x ln x,
+ *      f(0) = f(1) = 0, summed in exactly that order in double; IG = 0 when
+ *      every D_c = n L_c - N_c nL is 0 (the split carries no information).
+ *      ln is evaluated by a stated method so that any IEEE machine gets the
+ *      same bits: x = 2^e m with m in [sqrt(1/2), sqrt(2)) (exponent and
+ *      mantissa from the bit pattern), s = (m-1)/(m+1), ln m = 2 s P(s^2)
+ *      with P(z) = sum_{k=0}^{11} z^k / (2k+1) by Horner (the atanh series,
+ *      Abramowitz & Stegun 4.1.27), ln x = e ln2 + ln m.  Argmax, ties and
+ *      validity (best IG > 0) as R5.
  */
 #include <math.h>
 #include <stdint.h>
@@ -217,6 +226,61 @@ double orc_gini_gain(const int64_t *L, const int64_t *N, int C, int64_t n, int64
     return g / ((double)n * (double)n);
 }
 
+/* R15: natural log of a positive normal double by the atanh series. */
+double orc_ln(double x)
+{
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    int e = (int)((b >> 52) & 0x7ff) - 1022;
+    uint64_t mb = (b & 0x000FFFFFFFFFFFFFULL) | 0x3FE0000000000000ULL; /* m in [0.5, 1) */
+    double m;
+    memcpy(&m, &mb, sizeof m);
+    if (m < sqrt(0.5)) {
+        m = m * 2.0;
+        e = e - 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double P = 1.0 / 23.0;
+    for (int k = 10; k >= 0; k--)
+        P = P * z + 1.0 / (double)(2 * k + 1);
+    return (double)e * M_LN2 + (2.0 * s) * P;
+}
+
+/* R15: x ln x of a count. */
+double orc_xlnx(int64_t x)
+{
+    return x < 2 ? 0.0 : (double)x * orc_ln((double)x);
+}
+
+/* R15: information gain of a candidate with left class counts L out of
+ * node counts N (n = sum N, nL = sum L), one fixed double expression. */
+double orc_entropy_gain(const int64_t *L, const int64_t *N, int C, int64_t n, int64_t nL)
+{
+    int informative = 0;
+    for (int c = 0; c < C; c++)
+        if (n * L[c] - N[c] * nL != 0)
+            informative = 1;
+    if (!informative)
+        return 0.0;
+    double t = orc_xlnx(n);
+    for (int c = 0; c < C; c++)
+        t = t - orc_xlnx(N[c]);
+    for (int c = 0; c < C; c++)
+        t = t + orc_xlnx(L[c]);
+    t = t - orc_xlnx(nL);
+    for (int c = 0; c < C; c++)
+        t = t + orc_xlnx(N[c] - L[c]);
+    t = t - orc_xlnx(n - nL);
+    return t / (double)n;
+}
+
+static double criterion_gain(int criterion, const int64_t *L, const int64_t *N, int C, int64_t n,
+                             int64_t nL)
+{
+    return criterion == 1 ? orc_entropy_gain(L, N, C, n, nL) : orc_gini_gain(L, N, C, n, nL);
+}
+
 /* R2: the B-1 boundaries t_1..t_{B-1} (t[j-1] holds t_j). */
 void orc_boundaries(float mn, float mx, int B, float *t)
 {
@@ -292,6 +356,7 @@ float orc_midpoint(float a, float b)
  * bin_rule 0: equal-width boundaries (R2); 1: random-width (R14) from the
  * node's key bin_key, projection p drawing from stream p_base + p (p_base is
  * nonzero only when a caller searches a sub-range of the node's projections).
+ * criterion 0: Gini decrease (R4); 1: information gain (R15).
  * Optional outputs (may be NULL):
  *   left_counts[C]   class counts of the chosen left child
  *   mm_out[2P]       per projection (min, max)            (histogram path)
@@ -304,14 +369,14 @@ int orc_split_search_rule(const float *X, int64_t ld, const uint8_t *y, int C,
                           const int32_t *idx, int64_t n, int P, const int32_t *ptr,
                           const int32_t *feat, const int8_t *sign, int B, int sort_below,
                           int hist_only, int bin_rule, uint64_t bin_key, int p_base,
-                          orc_split *out, int64_t *left_counts, float *mm_out,
+                          int criterion, orc_split *out, int64_t *left_counts, float *mm_out,
                           int32_t *hist_out, double *gains_out, float *bounds_out)
 {
     memset(out, 0, sizeof(*out));
     out->proj = -1;
     out->cand = -1;
     if (C < 1 || C > ORC_MAX_CLASSES || B < 2 || B > 256 || n < 0 || P < 0 ||
-        bin_rule < 0 || bin_rule > 1)
+        bin_rule < 0 || bin_rule > 1 || criterion < 0 || criterion > 1)
         return -1;
     int64_t N[ORC_MAX_CLASSES] = {0};
     for (int64_t i = 0; i < n; i++)
@@ -351,7 +416,7 @@ int orc_split_search_rule(const float *X, int64_t ld, const uint8_t *y, int C,
                 if (!(pairs[i].v < pairs[i + 1].v))
                     continue;
                 int64_t nL = i + 1;
-                double g = orc_gini_gain(L, N, C, n, nL);
+                double g = criterion_gain(criterion, L, N, C, n, nL);
                 if (g > best) {
                     best = g;
                     out->valid = 1;
@@ -397,7 +462,7 @@ int orc_split_search_rule(const float *X, int64_t ld, const uint8_t *y, int C,
                 }
                 double g = -1.0;
                 if (nL > 0 && nL < n) {
-                    g = orc_gini_gain(L, N, C, n, nL);
+                    g = criterion_gain(criterion, L, N, C, n, nL);
                     if (g > best) {
                         best = g;
                         out->valid = 1;
@@ -430,7 +495,7 @@ int orc_split_search(const float *X, int64_t ld, const uint8_t *y, int C,
                      float *mm_out, int32_t *hist_out, double *gains_out)
 {
     return orc_split_search_rule(X, ld, y, C, idx, n, P, ptr, feat, sign, B, sort_below,
-                                 hist_only, 0, 0, 0, out, left_counts, mm_out, hist_out,
+                                 hist_only, 0, 0, 0, 0, out, left_counts, mm_out, hist_out,
                                  gains_out, NULL);
 }
 
@@ -508,8 +573,8 @@ static int tree_reserve(orc_tree *t, int64_t cap_nodes, int C, int cap)
  */
 int orc_train_tree(const float *X, int64_t ld, int32_t d, const uint8_t *y, int C,
                    const int32_t *root_idx, int64_t n_root, int B, int sort_below,
-                   int hist_only, int bin_rule, int P, double lambda, int cap, uint64_t seed,
-                   int32_t tree_id, int32_t max_depth, orc_tree *out)
+                   int hist_only, int bin_rule, int criterion, int P, double lambda, int cap,
+                   uint64_t seed, int32_t tree_id, int32_t max_depth, orc_tree *out)
 {
     memset(out, 0, sizeof(*out));
     if (C < 1 || C > ORC_MAX_CLASSES || cap < 1 || cap > ORC_MAX_CAP || n_root < 1 || P < 1)
@@ -587,8 +652,8 @@ int orc_train_tree(const float *X, int64_t ld, int32_t d, const uint8_t *y, int 
             }
             orc_split sp;
             if (orc_split_search_rule(X, ld, y, C, seg, nd.cnt, P, ptr, cfeat, csign, B,
-                                      sort_below, hist_only, bin_rule, nd.key, 0, &sp, NULL,
-                                      NULL, NULL, NULL, NULL))
+                                      sort_below, hist_only, bin_rule, nd.key, 0, criterion, &sp,
+                                      NULL, NULL, NULL, NULL, NULL))
                 goto done;
             out->path[id] = (int8_t)sp.path;
             if (!sp.valid)
@@ -674,7 +739,7 @@ void orc_predict_tree(const orc_tree *t, const float *X, int64_t ld, const int32
 typedef struct {
     const float *X; int64_t ld; const uint8_t *y; int C; const int32_t *idx; int64_t n;
     int p0, p1; const int32_t *ptr; const int32_t *feat; const int8_t *sign;
-    int B, sort_below, hist_only, bin_rule; uint64_t bin_key;
+    int B, sort_below, hist_only, bin_rule, criterion; uint64_t bin_key;
     orc_split res; int64_t lc[ORC_MAX_CLASSES]; int rc;
 } orc_range_job;
 
@@ -683,16 +748,16 @@ static void *orc_range_run(void *arg)
     orc_range_job *j = (orc_range_job *)arg;
     j->rc = orc_split_search_rule(j->X, j->ld, j->y, j->C, j->idx, j->n, j->p1 - j->p0,
                                   j->ptr + j->p0, j->feat, j->sign, j->B, j->sort_below,
-                                  j->hist_only, j->bin_rule, j->bin_key, j->p0, &j->res, j->lc,
-                                  NULL, NULL, NULL, NULL);
+                                  j->hist_only, j->bin_rule, j->bin_key, j->p0, j->criterion,
+                                  &j->res, j->lc, NULL, NULL, NULL, NULL);
     return NULL;
 }
 
 int orc_split_search_mt(const float *X, int64_t ld, const uint8_t *y, int C,
                         const int32_t *idx, int64_t n, int P, const int32_t *ptr,
                         const int32_t *feat, const int8_t *sign, int B, int sort_below,
-                        int hist_only, int bin_rule, uint64_t bin_key, int n_threads,
-                        orc_split *out, int64_t *left_counts)
+                        int hist_only, int bin_rule, uint64_t bin_key, int criterion,
+                        int n_threads, orc_split *out, int64_t *left_counts)
 {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > P) n_threads = P > 0 ? P : 1;
@@ -706,7 +771,7 @@ int orc_split_search_mt(const float *X, int64_t ld, const uint8_t *y, int C,
         j->p1 = (int)((int64_t)P * (t + 1) / n_threads);
         j->ptr = ptr; j->feat = feat; j->sign = sign;
         j->B = B; j->sort_below = sort_below; j->hist_only = hist_only;
-        j->bin_rule = bin_rule; j->bin_key = bin_key;
+        j->bin_rule = bin_rule; j->bin_key = bin_key; j->criterion = criterion;
     }
     int started = 0;
     for (int t = 1; t < n_threads; t++) {

@@ -50,8 +50,14 @@ def lib():
         L.orc_split_search_rule.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
                                             C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
-                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                            C.c_void_p]
+                                            C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]
+        L.orc_ln.restype = C.c_double
+        L.orc_ln.argtypes = [C.c_double]
+        L.orc_xlnx.restype = C.c_double
+        L.orc_xlnx.argtypes = [C.c_int64]
+        L.orc_entropy_gain.restype = C.c_double
+        L.orc_entropy_gain.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_int64]
         L.orc_bin.restype = C.c_int
         L.orc_bin.argtypes = [C.c_void_p, C.c_int, C.c_float]
         L.orc_midpoint.restype = C.c_float
@@ -67,15 +73,15 @@ def lib():
         L.orc_train_tree.restype = C.c_int
         L.orc_train_tree.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int,
                                      C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
-                                     C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int32, C.c_int32,
-                                     C.c_void_p]
+                                     C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int32,
+                                     C.c_int32, C.c_void_p]
         L.orc_tree_free.restype = None
         L.orc_tree_free.argtypes = [C.c_void_p]
         L.orc_split_search_mt.restype = C.c_int
         L.orc_split_search_mt.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
                                           C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
-                                          C.c_void_p, C.c_void_p]
+                                          C.c_int, C.c_void_p, C.c_void_p]
         L.orc_predict_tree.restype = None
         L.orc_predict_tree.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                        C.c_int64, C.c_void_p]
@@ -173,6 +179,21 @@ def gini_gain(L, N, n: int, nL: int) -> float:
     return float(lib().orc_gini_gain(_p(L), _p(N), L.shape[0], n, nL))
 
 
+def ln(x: float) -> float:
+    """The entropy criterion's natural log (atanh series)."""
+    return float(lib().orc_ln(float(x)))
+
+
+def xlnx(x: int) -> float:
+    return float(lib().orc_xlnx(int(x)))
+
+
+def entropy_gain(L, N, n: int, nL: int) -> float:
+    L = _c(L, np.int64)
+    N = _c(N, np.int64)
+    return float(lib().orc_entropy_gain(_p(L), _p(N), L.shape[0], n, nL))
+
+
 def boundaries(mn: float, mx: float, B: int) -> np.ndarray:
     t = np.empty(B - 1, dtype=np.float32)
     lib().orc_boundaries(C.c_float(mn), C.c_float(mx), B, _p(t))
@@ -215,9 +236,10 @@ class SplitResult:
 def split_search(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
                  ptr: np.ndarray, feat: np.ndarray, sign: np.ndarray, n_bins: int = 256,
                  sort_below: int = 1024, hist_only: bool = False,
-                 want_debug: bool = False, bin_rule: int = 0, bin_key: int = 0) -> SplitResult:
+                 want_debug: bool = False, bin_rule: int = 0, bin_key: int = 0,
+                 criterion: int = 0) -> SplitResult:
     """bin_rule 0: equal-width boundaries; 1: random-width boundaries drawn
-    from the node key bin_key."""
+    from the node key bin_key.  criterion 0: Gini decrease; 1: information gain."""
     X = _c(X, np.float32)
     y = _c(y, np.uint8)
     idx = _c(idx, np.int32)
@@ -237,8 +259,8 @@ def split_search(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
     rc = lib().orc_split_search_rule(
         _p(X), X.shape[1], _p(y), n_classes, _p(idx), idx.shape[0], P, _p(ptr), _p(feat),
         _p(sign), n_bins, sort_below, int(bool(hist_only)), int(bin_rule),
-        C.c_uint64(bin_key & 0xFFFFFFFFFFFFFFFF), 0, C.byref(out), _p(lc), opt(mm), opt(hist),
-        opt(gains), opt(bounds))
+        C.c_uint64(bin_key & 0xFFFFFFFFFFFFFFFF), 0, int(criterion), C.byref(out), _p(lc), opt(mm),
+        opt(hist), opt(gains), opt(bounds))
     if rc:
         raise ValueError("orc_split_search_rule failed")
     return SplitResult(out.valid, out.proj, out.path, out.cand, np.float32(out.threshold),
@@ -248,7 +270,7 @@ def split_search(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
 def split_search_mt(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarray,
                     ptr: np.ndarray, feat: np.ndarray, sign: np.ndarray, n_bins: int = 256,
                     sort_below: int = 1024, hist_only: bool = False, n_threads: int = 1,
-                    bin_rule: int = 0, bin_key: int = 0) -> SplitResult:
+                    bin_rule: int = 0, bin_key: int = 0, criterion: int = 0) -> SplitResult:
     """split_search with the projections divided over n_threads host threads
     (same result; no debug outputs)."""
     X = _c(X, np.float32)
@@ -262,8 +284,8 @@ def split_search_mt(X: np.ndarray, y: np.ndarray, n_classes: int, idx: np.ndarra
     lc = np.zeros(n_classes, dtype=np.int64)
     rc = lib().orc_split_search_mt(_p(X), X.shape[1], _p(y), n_classes, _p(idx), idx.shape[0], P, _p(ptr),
                                    _p(feat), _p(sign), n_bins, sort_below, int(bool(hist_only)),
-                                   int(bin_rule), C.c_uint64(bin_key & 0xFFFFFFFFFFFFFFFF), n_threads,
-                                   C.byref(out), _p(lc))
+                                   int(bin_rule), C.c_uint64(bin_key & 0xFFFFFFFFFFFFFFFF), int(criterion),
+                                   n_threads, C.byref(out), _p(lc))
     if rc:
         raise ValueError("orc_split_search_mt failed")
     return SplitResult(out.valid, out.proj, out.path, out.cand, np.float32(out.threshold),
@@ -309,14 +331,15 @@ class Tree:
 def train_tree(X: np.ndarray, y: np.ndarray, n_classes: int, root_idx: np.ndarray, *,
                n_proj: int, lam: float, cap: int, n_bins: int = 256, sort_below: int = 1024,
                hist_only: bool = False, seed: int = 0, tree_id: int = 0,
-               max_depth: int = -1, bin_rule: int = 0) -> Tree:
+               max_depth: int = -1, bin_rule: int = 0, criterion: int = 0) -> Tree:
     X = _c(X, np.float32)
     y = _c(y, np.uint8)
     root_idx = _c(root_idx, np.int32)
     t = OrcTree()
     rc = lib().orc_train_tree(_p(X), X.shape[1], X.shape[0], _p(y), n_classes, _p(root_idx),
                               root_idx.shape[0], n_bins, sort_below, int(bool(hist_only)),
-                              int(bin_rule), n_proj, lam, cap, C.c_uint64(seed), tree_id, max_depth,
+                              int(bin_rule), int(criterion), n_proj, lam, cap, C.c_uint64(seed), tree_id,
+                              max_depth,
                               C.byref(t))
     if rc:
         raise RuntimeError("orc_train_tree failed")

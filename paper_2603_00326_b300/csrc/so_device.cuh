@@ -136,11 +136,11 @@ __device__ __forceinline__ float rw_boundary(uint32_t u, float mn, float w) {
   return __fadd_rn(mn, __fmul_rn(f, w));
 }
 // Guide cell of v: every step (one fused multiply-add, round down to an
-// integer, clamp) is monotone non-decreasing in v, so cell(t) < cell(v)
-// implies t < v and cell(t) > cell(v) implies t > v.  NaN maps to cell 0.
+// unsigned integer -- negative values and NaN saturate to 0 --, clamp above)
+// is monotone non-decreasing in v, so cell(t) < cell(v) implies t < v and
+// cell(t) > cell(v) implies t > v.
 __device__ __forceinline__ int rw_cell(float v, float s, float o) {
-  const int c = __float2int_rd(__fmaf_rn(v, s, o));
-  return min(max(c, 0), kRwCells - 1);
+  return (int)min(__float2uint_rd(__fmaf_rn(v, s, o)), (unsigned)(kRwCells - 1));
 }
 // Upper-bound count #{j < nb : t[j] <= v} by binary search (any rule).
 __device__ __forceinline__ int bin_search(const float* __restrict__ t, int nb, float v) {

@@ -87,26 +87,27 @@ __device__ __forceinline__ unsigned lds_u16(unsigned a) {
   asm volatile("ld.shared.u16 %0, [%1];\n" : "=h"(v) : "r"(a));
   return v;
 }
-__device__ __forceinline__ unsigned lds_u8(unsigned a) {
-  unsigned short v;
-  asm volatile("ld.shared.u8 %0, [%1];\n" : "=h"(v) : "r"(a));
-  return v;
-}
 __device__ __forceinline__ float lds_f32(unsigned a) { return __uint_as_float(lds_u32(a)); }
 __device__ __forceinline__ void reds_add(unsigned a, unsigned v) {
   asm volatile("red.shared.add.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
 }
 
 // Random-width bin #{j < nb : t_j <= v} over a projection's sorted boundaries
-// at shared address tb.  GUIDED: start at the guide's count for v's cell (a
-// lower bound of the bin) and step up while the next boundary is <= v; the
-// guide at gb and the cell map (s, o) come from so_rw.cu.  Otherwise a binary
-// search.  Both loops are bounded by nb.
+// at shared address tb.  GUIDED: v's cell holds lo (boundaries of lower
+// cells, all below v) and k (boundaries in the cell, t_lo .. t_{lo+k-1}); the
+// bin is lo plus those of the k that are <= v.  The first two are compared
+// without a branch (the second read may pass the row end when k < 2: it
+// stays inside the table area of shared memory and is masked); cells with
+// more than two boundaries (8% of cells) finish in a loop bounded by k.
+// Otherwise a binary search bounded by nb.
 template <bool GUIDED>
 __device__ __forceinline__ int rw_bin_smem(float v, float s, float o, unsigned tb, unsigned gb, int nb) {
   if (GUIDED) {
-    int b = (int)lds_u8(gb + (unsigned)rw_cell(v, s, o));
-    while (b < nb && lds_f32(tb + 4u * (unsigned)b) <= v) ++b;
+    const unsigned g = lds_u16(gb + 2u * (unsigned)rw_cell(v, s, o));
+    const unsigned lo = g & 0xffu, k = g >> 8;
+    const unsigned ta = tb + 4u * lo;
+    int b = (int)lo + ((k > 0u && lds_f32(ta) <= v) ? 1 : 0) + ((k > 1u && lds_f32(ta + 4u) <= v) ? 1 : 0);
+    for (unsigned i = 2; i < k; ++i) b += lds_f32(ta + 4u * i) <= v ? 1 : 0;
     return b;
   }
   int lo = 0, hi = nb;
@@ -973,7 +974,7 @@ __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* 
       if (pls[sl] >= 0) {
         const unsigned dpk = su32(s_dpk) + 4u * pls[sl] * kmax;
         if (RW) {
-          const unsigned tb = rwt + 4u * kRwRow * pls[sl], gb = rwg + kRwRow * pls[sl];
+          const unsigned tb = rwt + 4u * kRwRow * pls[sl], gb = rwg + 2u * kRwRow * pls[sl];
           if (bps[sl].fast)
             hist_tile_rw<V, NQ, true>(tile, lab, dpk, ks[sl], lane, bps[sl], tb, gb, B - 1, C4, limit_abs);
           else
@@ -1022,7 +1023,7 @@ __device__ __forceinline__ void hist_item_buf(const float* __restrict__ vbuf, in
         for (int w = 0; w < 4; ++w) yo[4 * u + w] = label_off8((lw >> (8 * w)) & 0xffu);
       }
       if (RW) {
-        const unsigned tb = rwt + 4u * kRwRow * pl, gb = rwg + kRwRow * pl;
+        const unsigned tb = rwt + 4u * kRwRow * pl, gb = rwg + 2u * kRwRow * pl;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const unsigned b = (unsigned)(bp.fast ? rw_bin_smem<true>(v[i], bp.mn, bp.W, tb, gb, B - 1)
@@ -1067,8 +1068,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   int* s_yo = reinterpret_cast<int*>(s_lab + kMaxItem + 512);                // [3][256] tile label offsets
   uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_yo + 3 * 256);            // [hist_words]
   float* s_rwt = reinterpret_cast<float*>(s_hist + hist_words);              // RW: [PG][kRwRow] boundaries
-  uint8_t* s_rwg = reinterpret_cast<uint8_t*>(s_rwt + (RW ? PG * kRwRow : 0));  // RW: [PG][kRwRow] guide
-  uint32_t* s_dpk = reinterpret_cast<uint32_t*>(s_rwg + (RW ? PG * kRwRow : 0));  // [kHistPGMax*KMAX]
+  uint16_t* s_rwg = reinterpret_cast<uint16_t*>(s_rwt + (RW ? PG * kRwRow : 0));  // RW: [PG][kRwRow] guide
+  uint32_t* s_dpk = reinterpret_cast<uint32_t*>(s_rwg + (RW ? PG * kRwRow : 0));   // [kHistPGMax*KMAX]
   int* s_dk = reinterpret_cast<int*>(s_dpk + kHistPGMax * KMAX);             // [kHistPGMax]
   int* s_assign = s_dk + kHistPGMax;                                         // [kHistPGMax]
   int* s_rowfeat = s_assign + kHistPGMax;                                    // [kStUMax]
@@ -1111,7 +1112,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
       int4* st4 = reinterpret_cast<int4*>(s_rwt);
       int4* sg4 = reinterpret_cast<int4*>(s_rwg);
       for (int e = threadIdx.x; e < it.np * (kRwRow / 4); e += kStThreads) st4[e] = gt[e];
-      for (int e = threadIdx.x; e < it.np * (kRwRow / 16); e += kStThreads) sg4[e] = gg[e];
+      for (int e = threadIdx.x; e < it.np * (kRwRow / 8); e += kStThreads) sg4[e] = gg[e];
       if (threadIdx.x < it.np) {
         const int pl = threadIdx.x;
         const float2 so = rw.so[it.h * P + it.p0 + pl];
@@ -1182,7 +1183,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
           const int yv = ds.y[s];
           int b;
           if (RW) {
-            const unsigned tb = su32(s_rwt) + 4u * kRwRow * pl, gb = su32(s_rwg) + kRwRow * pl;
+            const unsigned tb = su32(s_rwt) + 4u * kRwRow * pl, gb = su32(s_rwg) + 2u * kRwRow * pl;
             b = bf.x >= 0.0f ? rw_bin_smem<true>(acc, bf.x, bf.y, tb, gb, B - 1)
                              : rw_bin_smem<false>(acc, bf.x, bf.y, tb, gb, B - 1);
           } else {
@@ -1211,10 +1212,14 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
 // ---- host side ----------------------------------------------------------------
 int hist_group_size(int B, int C, bool rw) {
   // 16-bit counters, two projections per word, plus the random-width tables
-  // (boundaries and guide of each projection), in <= 100 KB of shared memory
-  const int pair_bytes = (B + 1) * C * 4 + (rw ? 2 * kRwRow * 5 : 0);
+  // (boundaries and guide of each projection), in <= 100 KB of shared memory.
+  // Rounded down to a multiple of the 32 warps when at least 32: a group of,
+  // say, 36 gives 4 warps two projections while 28 wait at every barrier.
+  const int pair_bytes = (B + 1) * C * 4 + (rw ? 2 * kRwRow * 6 : 0);
   int pg = 2 * ((100 * 1024) / pair_bytes);
-  return pg < 1 ? 1 : (pg > kHistPGMax ? kHistPGMax : pg);
+  if (pg >= kHistPGMax) return kHistPGMax;
+  if (pg >= kStWarps) return kStWarps;
+  return pg < 1 ? 1 : pg;
 }
 
 // The feature bitmap (2 * ceil(d/32) words <= 16 KB) lives in the third tile
@@ -1227,7 +1232,7 @@ size_t mm_smem_bytes(int /*d*/, int kmax) {
 size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG, bool rw) {
   const int npair = (PG + 1) >> 1;
   const size_t hist_words = ((size_t)npair * (B + 1) * C + 1 + 3) & ~(size_t)3;
-  const size_t rw_bytes = rw ? (size_t)PG * kRwRow * 5 : 0;
+  const size_t rw_bytes = rw ? (size_t)PG * kRwRow * 6 : 0;
   return (size_t)3 * kTileF * 4 + kMaxItem + 512 + 3 * 256 * 4 + hist_words * 4 + rw_bytes +
          (size_t)kHistPGMax * kmax * 4 + kHistPGMax * 8 + kStUMax * 12;
 }

@@ -72,13 +72,14 @@ struct HistTuning {
 // Random-width boundary tables of the histogram nodes (one row of kRwRow per
 // histogram slot h and projection p, row h*P + p):
 //  t   boundaries t_1..t_{B-1}, ascending, padded with +inf;
-//  g   guide: g[c] = number of boundaries whose cell is below c (cells of the
-//      monotone map v -> clamp(floor(fma(v, s, o)), 0, kRwCells-1));
+//  g   guide of cell c: lo | (k << 8), lo = number of boundaries whose cell
+//      is below c, k = number of boundaries in cell c (cells of the monotone
+//      map v -> clamp(floor(fma(v, s, o)), 0, kRwCells-1));
 //  so  (s, o) of that map; s < 0 marks a projection without a guide (zero or
 //      ill-conditioned range), binned by binary search.
 struct RwTables {
   float* t = nullptr;
-  uint8_t* g = nullptr;
+  uint16_t* g = nullptr;
   float2* so = nullptr;
 };
 

@@ -532,7 +532,7 @@ void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int3
   carve_staged(cv, s.staged, mh, P);
   if (bin_rule == SO_BINS_RANDOM_WIDTH) {
     s.rw.t = cv.take<float>((size_t)mh * P * kRwRow);
-    s.rw.g = cv.take<uint8_t>((size_t)mh * P * kRwRow);
+    s.rw.g = cv.take<uint16_t>((size_t)mh * P * kRwRow);
     s.rw.so = cv.take<float2>((size_t)mh * P);
   } else {
     s.rw = RwTables{};

@@ -9,12 +9,12 @@
 //  3. places t_j = min + ((2u+1) 2^-24) * (max - min), float, two roundings;
 //  4. builds the guide of the histogram kernels: for the monotone cell map
 //     v -> clamp(floor(fma(v, s, o)), 0, 255) with s = 256 / (max - min) and
-//     o = -min * s, g[c] = #{ j : cell(t_j) < c }.  A value v then has at
-//     least g[cell(v)] boundaries at or below it (each of those lies in a
-//     lower cell, so below v) and none of the boundaries in higher cells, so
-//     its bin is found by scanning the sorted boundaries from g[cell(v)] while
-//     they are <= v.  Boundaries are uniform over the range, so a cell holds
-//     one boundary on average.
+//     o = -min * s, cell c stores lo = #{ j : cell(t_j) < c } and the count k
+//     of boundaries with cell(t_j) == c (those are t_lo .. t_{lo+k-1}).  A
+//     value v in cell c has every boundary of a lower cell below it and every
+//     boundary of a higher cell above it, so its bin is lo plus the number of
+//     the cell's k boundaries that are <= v.  Boundaries are uniform over the
+//     range, so k is 0, 1 or 2 for 92% of cells.
 // Projections whose range is zero or tiny against its magnitude (boundaries
 // that round onto a few floats) get no guide (s = -1) and are binned by
 // binary search; the bin is the same either way.
@@ -78,9 +78,9 @@ __global__ void __launch_bounds__(kRwWarps * 32) k_rw_bounds(const V4* plan_tota
       cell[j] = (uint8_t)((guided && j < nb) ? rw_cell(t, s, o) : kRwCells - 1);
     }
     __syncwarp();
-    // cells ascend with j (sorted boundaries, monotone map): g[c] is the
-    // first j whose cell is >= c
-    uint8_t* grow = rw.g + wi * kRwRow;
+    // cells ascend with j (sorted boundaries, monotone map): the first j
+    // whose cell is >= c, and the first whose cell is > c
+    uint16_t* grow = rw.g + wi * kRwRow;
     for (int c = lane; c < kRwCells; c += 32) {
       int lo = 0, hi = nb;
       while (lo < hi) {
@@ -88,7 +88,13 @@ __global__ void __launch_bounds__(kRwWarps * 32) k_rw_bounds(const V4* plan_tota
         if ((int)cell[mid] < c) lo = mid + 1;
         else hi = mid;
       }
-      grow[c] = (uint8_t)(guided ? lo : 0);
+      int up = lo, hi2 = nb;
+      while (up < hi2) {
+        const int mid = (up + hi2) >> 1;
+        if ((int)cell[mid] <= c) up = mid + 1;
+        else hi2 = mid;
+      }
+      grow[c] = guided ? (uint16_t)(lo | ((up - lo) << 8)) : (uint16_t)0;
     }
     if (lane == 0) rw.so[wi] = make_float2(s, o);
     __syncwarp();  // the next iteration rewrites u and cell

@@ -56,7 +56,7 @@ def choose_nodes(gt, n_internal=12, n_leaves=6, seed=0):
 
 
 def route_and_sample(gt, X, y, C, root, *, n_proj, lam, cap, n_bins=256, sort_below=1024, hist_only=False,
-                     seed=0, tree_id=0, max_depth=-1, check_ids=None, bin_rule=0):
+                     seed=0, tree_id=0, max_depth=-1, check_ids=None, bin_rule=0, criterion=0):
     """Checks the GPU tree `gt` against the oracle; returns the number of
     nodes re-searched."""
     X = np.ascontiguousarray(X, dtype=np.float32)
@@ -83,7 +83,7 @@ def route_and_sample(gt, X, y, C, root, *, n_proj, lam, cap, n_bins=256, sort_be
             nnz, feat, sign = O.sample_node(key, n_proj, d, lam, cap)
             ptr, f, sg = O.slots_to_csr(nnz, feat, sign)
             r = O.split_search(X, y, C, s, ptr, f, sg, n_bins=n_bins, sort_below=sort_below, hist_only=hist_only,
-                               bin_rule=bin_rule, bin_key=key)
+                               bin_rule=bin_rule, bin_key=key, criterion=criterion)
             searched += 1
             assert int(gt.path[v]) == r.path, (ctx, int(gt.path[v]), r.path)
             assert (not leaf) == bool(r.valid), ctx
