@@ -273,7 +273,15 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
             out["forest_2m"]["random_width_tree0"] = {
                 "train_s": rsecs, "nodes": rtrees[0].n_nodes, "depth": int(rtrees[0].depth.max()),
                 "oob_accuracy": float((p1.cpu().numpy()[~inbag] == fs.y[~inbag]).mean())}
-            del rtrees
+            # and with the entropy criterion (information gain, YDF's)
+            ecfg = dataclasses.replace(cfg, n_trees=1, criterion=S.SO_CRIT_ENTROPY)
+            torch.cuda.synchronize()
+            etrees, esecs = F.train_forest(ecfg, dd)
+            p1, _ = S.so_predict(dd.X, S.upload_forest(etrees, 2))
+            out["forest_2m"]["entropy_tree0"] = {
+                "train_s": esecs, "nodes": etrees[0].n_nodes, "depth": int(etrees[0].depth.max()),
+                "oob_accuracy": float((p1.cpu().numpy()[~inbag] == fs.y[~inbag]).mean())}
+            del rtrees, etrees
         del dd, trees, fo
     if wide_trees > 0 and only in (None, "wide"):
         # wide count-like data: n=500k, d=4096, 90% zeros, 5 classes, grown to purity
@@ -316,13 +324,17 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
     return out
 
 
-def random_width_step(S, torch, ds, pj, idx, off, n, P, C, n_bins, steps, key):
-    """The root step (search + partition) with random-width bins (the YDF
-    default of the paper's Section 1 footnote) on resident inputs: CUDA-event
-    time per step and per-stage times, with the histogram kernel's roofline."""
+def variant_step(S, torch, ds, pj, idx, off, n, P, C, n_bins, steps, key=None, criterion=0):
+    """The root step (search + partition) on resident inputs with random-width
+    bins (key given: the YDF default of the paper's Section 1 footnote) or
+    another criterion (1: information gain, YDF's): CUDA-event time per step
+    and per-stage times."""
     dev = idx.device
-    keys = torch.tensor([key], dtype=torch.int64, device=dev)
-    prm = S.split_params(n_bins, 0, True, bin_rule=S.SO_BINS_RANDOM_WIDTH, bin_keys=keys)
+    if key is not None:
+        keys = torch.tensor([key], dtype=torch.int64, device=dev)
+        prm = S.split_params(n_bins, 0, True, bin_rule=S.SO_BINS_RANDOM_WIDTH, bin_keys=keys, criterion=criterion)
+    else:
+        prm = S.split_params(n_bins, 0, True, criterion=criterion)
     ws = torch.empty(S.so_split_search_ws_bytes(1, n, P, C, prm), dtype=torch.uint8, device=dev)
     out = torch.empty(S.SPLIT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     lc = torch.empty(C, dtype=torch.int64, device=dev)
@@ -367,10 +379,11 @@ def run_leg(args):
                            torch.from_numpy(pr.sign).to(dev), int(np.diff(pr.ptr).max()))
         idx = torch.arange(n, dtype=torch.int32, device=dev)
         off = torch.tensor([0, n], dtype=torch.int64, device=dev)
-        res = random_width_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, rw_key())
+        res = variant_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, key=rw_key())
         res.update(_rw_roofline(pr, n, res["stage_ms_per_launch"].get("k_hist")))
+        ent = variant_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, criterion=1)
         del ds, pj, idx
-        out = {"root_4m_random_width": res}
+        out = {"root_4m_random_width": res, "root_4m_entropy": ent}
         if args.forest_trees > 0:
             out.update(extra_legs(S, torch, dev, 1, only="forest", rw_tree=True))
         print(json.dumps({"leg": args.leg, **out}), flush=True)
@@ -565,9 +578,10 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_extras:
         # the same step with random-width bins, on the resident inputs
-        rw = random_width_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, rw_key())
+        rw = variant_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, key=rw_key())
         rw.update(_rw_roofline(pr, n, rw["stage_ms_per_launch"].get("k_hist")))
         line["random_width"] = rw
+        line["entropy"] = variant_step(S, torch, ds, pj, idx, off, n, P, C, p["n_bins"], args.steps, criterion=1)
         line["extras"] = extra_legs(S, torch, dev, args.forest_trees, wide_trees=args.wide_trees)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()

@@ -86,6 +86,9 @@ typedef struct {
 /* Histogram boundary rules (so_split_params.bin_rule). */
 enum { SO_BINS_EQUAL_WIDTH = 0, SO_BINS_RANDOM_WIDTH = 1 };
 
+/* Split criteria (so_split_params.criterion). */
+enum { SO_CRIT_GINI = 0, SO_CRIT_ENTROPY = 1 };
+
 /* Split-search parameters.
  *  n_bins       bins per projection, 2..256 (Section 3.2 uses 256).
  *  sort_below   T: nodes with fewer than T samples take the exact sort path
@@ -106,6 +109,16 @@ enum { SO_BINS_EQUAL_WIDTH = 0, SO_BINS_RANDOM_WIDTH = 1 };
  *               draws B-1 outputs r; their top 23 bits u = r >> 41, sorted
  *               ascending, place t_j = min + f_j*(max-min) with
  *               f_j = (2u+1)*2^-24 (float, two roundings).
+ *  criterion    SO_CRIT_GINI: Gini decrease sum_c D_c^2 / (n^2 nL nR),
+ *               D_c = n L_c - N_c nL.  SO_CRIT_ENTROPY: information gain in
+ *               nats (the entropy criterion of YDF, Section 3 step 3):
+ *               (f(n) - sum_c f(N_c) + sum_c f(L_c) - f(nL) + sum_c f(R_c)
+ *               - f(nR)) / n with f(x) = x ln x, in double in that order, 0
+ *               when every D_c is 0; ln x = e ln2 + 2s sum_{k<12} s^2k/(2k+1)
+ *               with x = 2^e m, m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1)
+ *               (so the bits are the same on any IEEE machine).  Either way
+ *               the best split maximises the double gain (ties to the lowest
+ *               projection, then candidate) and is valid iff that gain is > 0.
  *  bin_keys     SO_BINS_RANDOM_WIDTH: device uint64 [m], the key of each node
  *               of the call (node j of a batch reads bin_keys[j]; a one-node
  *               call reads bin_keys[0]); the same keys so_sample_projections
@@ -116,11 +129,12 @@ typedef struct {
     int32_t hist_only;
     float rescore_rel_eps;
     int32_t bin_rule;
+    int32_t criterion;
     const uint64_t *bin_keys;
 } so_split_params;
 
 /* Result of one node's split search.
- *  valid      1 iff a split with Gini decrease > 0 exists.
+ *  valid      1 iff a split with criterion gain > 0 exists.
  *  proj       winning projection (row within the node), or -1.
  *  path       0 histogram, 1 exact sort: the path the node's size selects
  *             (also reported for nodes of fewer than 2 samples, which are
@@ -129,8 +143,9 @@ typedef struct {
  *  cand       histogram path: bin b (bins <= b go left); sort path: sorted
  *             position i (the i+1 smallest values go left); -1 if invalid.
  *  threshold  samples with projected value < threshold go left.
- *  gain       Gini decrease sum_c D_c^2 / (n^2 nL nR), D_c = n L_c - N_c nL,
- *             evaluated in double (bit-identical to the CPU definition).
+ *  gain       the criterion's gain (Gini decrease or information gain, see
+ *             so_split_params) evaluated in double (bit-identical to the CPU
+ *             definition).
  *  n_left / n_right  child sizes (counting repeated samples). */
 typedef struct {
     int32_t valid;
@@ -253,8 +268,9 @@ so_status so_histograms(const so_dataset *ds, const int32_t *idx, int64_t n_tota
                         float *gain32_dev, float *bounds_dev, void *stream);
 
 /* Tree growth parameters.
- *  n_bins, sort_below, hist_only, rescore_rel_eps, bin_rule  as in
- *             so_split_params; random-width boundaries use the tree's node keys.
+ *  n_bins, sort_below, hist_only, rescore_rel_eps, bin_rule, criterion  as
+ *             in so_split_params; random-width boundaries use the tree's node
+ *             keys.
  *  n_proj     projections sampled per node, 1..1024.
  *  lambda, nnz_cap  nnz law of a projection: min(nnz_cap, d, 1+Poisson(lambda)).
  *  seed, tree_id    root key = splitmix64(seed ^ tree_id*0x9E3779B97F4A7C15);
@@ -272,6 +288,7 @@ typedef struct {
     int32_t tree_id;
     int32_t max_depth;
     int32_t bin_rule;
+    int32_t criterion;
 } so_tree_params;
 
 /* A trained tree in breadth-first order (children appended level by level in

@@ -128,6 +128,8 @@ so_status check_params(const so_split_params* p, bool keys_given = true) {
     return fail(SO_EINVAL, "bin_rule=%d is neither equal width (0) nor random width (1)", p->bin_rule);
   if (keys_given && p->bin_rule == SO_BINS_RANDOM_WIDTH && !p->bin_keys)
     return fail(SO_EINVAL, "random-width bins need bin_keys");
+  if (p->criterion != SO_CRIT_GINI && p->criterion != SO_CRIT_ENTROPY)
+    return fail(SO_EINVAL, "criterion=%d is neither Gini (0) nor entropy (1)", p->criterion);
   return SO_OK;
 }
 
@@ -300,6 +302,7 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     a.left_counts = left_counts_dev;
     a.bin_rule = params->bin_rule;
     a.bin_keys = params->bin_keys;
+    a.criterion = params->criterion;
     SO_CK(launch_search(a, s, cs));
     return SO_OK;
   });
@@ -355,6 +358,7 @@ so_status so_split_search(const so_dataset* ds, const int32_t* idx, int64_t n_no
     a.left_counts = lc;
     a.bin_rule = params->bin_rule;
     a.bin_keys = params->bin_keys;
+    a.criterion = params->criterion;
     SO_CK(launch_search(a, s, cs));
     int64_t lch[kMaxClasses];
     SO_CK(cudaMemcpyAsync(out_host, out_dev, sizeof(so_split), cudaMemcpyDeviceToHost, cs));
@@ -567,7 +571,8 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
     memset(out, 0, sizeof(*out));
     if (n_root < 1 || n_root > INT32_MAX / 2) return fail(SO_EINVAL, "n_root out of range");
     if (!root_idx) return fail(SO_EINVAL, "root_idx is NULL");
-    so_split_params sp{tp->n_bins, tp->sort_below, tp->hist_only, tp->rescore_rel_eps, tp->bin_rule, nullptr};
+    so_split_params sp{tp->n_bins,   tp->sort_below, tp->hist_only, tp->rescore_rel_eps,
+                       tp->bin_rule, tp->criterion,  nullptr};
     if ((st = check_params(&sp, false))) return st;
     if (tp->n_proj < 1 || tp->n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj outside 1..1024");
     if (tp->nnz_cap < 1 || tp->nnz_cap > kMaxCap) return fail(SO_EINVAL, "nnz_cap outside 1..32");
@@ -730,6 +735,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
           a.vbuf = vbuf;
           a.bin_rule = tp->bin_rule;
           a.bin_keys = cur.key + j0;  // random-width boundaries from the node keys
+          a.criterion = tp->criterion;
           e = launch_search(a, ss, ls);
           if (e == cudaSuccess)
             e = launch_tree_record_splits((int32_t)j0, mb, cur, spl, snnz, sfeat, ssign, P, cap, td, ls);
@@ -938,6 +944,7 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
         a.vbuf = m > 1 ? vbuf : nullptr;
         a.bin_rule = params->bin_rule;
         a.bin_keys = keys;
+        a.criterion = params->criterion;
         SO_CK(launch_search(a, ss, cs));  // warm-up
         SO_CK(cudaEventRecord(e0, cs));
         const int reps = 3;

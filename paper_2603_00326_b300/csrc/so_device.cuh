@@ -180,6 +180,120 @@ __device__ __forceinline__ T warp_incl_scan(T v, int lane) {
   return v;
 }
 
+// ---- information gain (entropy criterion, the YDF learner's, Section 3 step 3)
+// Definition in double, fixed order: t = f(n) - sum_c f(N_c) + sum_c f(L_c)
+// - f(nL) + sum_c f(R_c) - f(nR), IG = t / n, f(x) = x ln x; IG = 0 when
+// every D_c = n L_c - N_c nL is 0.  ln by a stated method so that any IEEE
+// machine gets the same bits: x = 2^e m, m in [sqrt(1/2), sqrt(2)) from the
+// bit pattern, s = (m-1)/(m+1), ln m = 2 s P(s^2) with the atanh series
+// P(z) = sum_{k<12} z^k/(2k+1) by Horner, ln x = e ln2 + ln m.
+constexpr double kLn2 = 0x1.62e42fefa39efp-1;       // ln 2 rounded to double
+constexpr double kSqrtHalf = 0x1.6a09e667f3bcdp-1;  // sqrt(1/2) rounded to double
+constexpr int kXlnxTab = 2048;                      // table of x ln x, x < 2048 (exact-path counts)
+
+__device__ __forceinline__ double ln_series(double x) {
+  // 1/(2k+1) rounded to double, k = 0..11
+  constexpr double kC[12] = {0x1p+0,
+                             0x1.5555555555555p-2,
+                             0x1.999999999999ap-3,
+                             0x1.2492492492492p-3,
+                             0x1.c71c71c71c71cp-4,
+                             0x1.745d1745d1746p-4,
+                             0x1.3b13b13b13b14p-4,
+                             0x1.1111111111111p-4,
+                             0x1.e1e1e1e1e1e1ep-5,
+                             0x1.af286bca1af28p-5,
+                             0x1.8618618618618p-5,
+                             0x1.642c8590b2164p-5};
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((bits >> 52) & 0x7ffull) - 1022;
+  double m = __longlong_as_double((long long)((bits & 0x000FFFFFFFFFFFFFull) | 0x3FE0000000000000ull));
+  if (m < kSqrtHalf) {
+    m = __dmul_rn(m, 2.0);
+    e -= 1;
+  }
+  const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+  const double z = __dmul_rn(s, s);
+  double P = kC[11];
+#pragma unroll
+  for (int k = 10; k >= 0; --k) P = __dadd_rn(__dmul_rn(P, z), kC[k]);
+  return __dadd_rn(__dmul_rn((double)e, kLn2), __dmul_rn(__dmul_rn(2.0, s), P));
+}
+__device__ __forceinline__ double xlnx64(long long x) {
+  return x < 2 ? 0.0 : __dmul_rn(__ll2double_rn(x), ln_series(__ll2double_rn(x)));
+}
+__device__ __forceinline__ double xlnx_t(long long x, const double* tab) {
+  return (tab && x < kXlnxTab) ? tab[x] : xlnx64(x);
+}
+__device__ __forceinline__ bool informative(const int* L, const int* N, int C, int64_t n, int64_t nL) {
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) any |= (n * (long long)L[c] - (long long)N[c] * nL) != 0;
+  return any;
+}
+__device__ __forceinline__ double ent_gain64(const int* L, const int* N, int C, int64_t n, int64_t nL,
+                                             const double* tab) {
+  if (!informative(L, N, C, n, nL)) return 0.0;
+  double t = xlnx_t(n, tab);
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) t = __dsub_rn(t, xlnx_t(N[c], tab));
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) t = __dadd_rn(t, xlnx_t(L[c], tab));
+  t = __dsub_rn(t, xlnx_t(nL, tab));
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) t = __dadd_rn(t, xlnx_t((long long)N[c] - L[c], tab));
+  t = __dsub_rn(t, xlnx_t(n - nL, tab));
+  return __ddiv_rn(t, __ll2double_rn(n));
+}
+// Float comparison key of the information gain: n IG / ln 2 without the node
+// constant, sum_c (L_c lg L_c + R_c lg R_c) - nL lg nL - nR lg nR (lg = log2
+// by the fast intrinsic: 2^-22 absolute error on [0.5, 2], 2 ulp elsewhere).
+// Candidates without information are -inf.
+__device__ __forceinline__ float xlg2x(long long x) {
+  const float xf = __ll2float_rn(x);
+  return x < 2 ? 0.0f : __fmul_rn(xf, __log2f(xf));
+}
+__device__ __forceinline__ float ent_key32(const int* L, const int* N, int C, int64_t n, int64_t nL) {
+  if (!informative(L, N, C, n, nL)) return -INFINITY;
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) s = __fadd_rn(__fadd_rn(s, xlg2x(L[c])), xlg2x((long long)N[c] - L[c]));
+  return __fsub_rn(__fsub_rn(s, xlg2x(nL)), xlg2x(n - nL));
+}
+// Re-score window of the key at a node of n samples: every candidate's key
+// is within E of its double gain (same units), with m = 2C+2 terms of size at
+// most F = n log2 n (all terms sum to at most 2F), per-term error 2^-21
+// relative plus 2^-20 absolute, float summation m 2^-24 relative:
+// E <= F (2C+10) 2^-23 + (2C+2) 2^-20.  The double winner (and every double
+// tie of it) lies within 2E of the float maximum; the window is 3E.
+__device__ __forceinline__ float ent_window(int64_t n, int C) {
+  const float nf = __ll2float_rn(n);
+  const float F = __fmul_rn(__fmul_rn(nf, __log2f(nf) + 0.01f), 1.01f) + 2.0f;
+  return 3.0f * (F * (float)(2 * C + 10) * 0x1p-23f + (float)(2 * C + 2) * 0x1p-20f);
+}
+
+// The split criterion as the kernels use it (Crit, so_internal.h): a float
+// key for every candidate, the re-score window around the float maximum, the
+// double gain.
+__device__ __forceinline__ float key32(const Crit& cr, const int* L, const int* N, int C, int64_t n, int64_t nL) {
+  return cr.ent ? ent_key32(L, N, C, n, nL) : gain32(L, N, C, n, nL);
+}
+__device__ __forceinline__ double gain64c(const Crit& cr, const int* L, const int* N, int C, int64_t n,
+                                          int64_t nL) {
+  return cr.ent ? ent_gain64(L, N, C, n, nL, cr.tab) : gain64(L, N, C, n, nL);
+}
+// key of "no candidate"; whether a float maximum has a candidate that can win
+__device__ __forceinline__ float key_none(const Crit& cr) { return cr.ent ? -INFINITY : -1.0f; }
+__device__ __forceinline__ bool key_any(const Crit& cr, float M) { return cr.ent ? M > -INFINITY : M > 0.0f; }
+__device__ __forceinline__ float key_thr(const Crit& cr, float M, int64_t n, int C) {
+  return cr.ent ? __fsub_rn(M, ent_window(n, C)) : __fmul_rn(M, 1.0f - cr.eps);
+}
+
 // A candidate of the double re-score, ordered by (gain desc, proj asc, cand asc).
 struct Cand {
   double g;

@@ -107,6 +107,7 @@ struct SearchArgs {
   // SO_BINS_EQUAL_WIDTH or SO_BINS_RANDOM_WIDTH; node keys of the random rule
   int32_t bin_rule = 0;
   const uint64_t* bin_keys = nullptr;  // device [m]
+  int32_t criterion = 0;               // SO_CRIT_GINI or SO_CRIT_ENTROPY
   // optional [P][n_total] buffer: the min / max pass stores every
   // histogram-path sample's projected values and the histogram pass reads
   // them back instead of gathering the feature columns again
@@ -142,6 +143,7 @@ struct SearchScratch {
   int64_t m_hist_cap = 0;
   StagedScratch staged;
   RwTables rw;                  // random-width rule only
+  double* xlnx = nullptr;       // [2048] x ln x of the entropy criterion
 };
 
 // Carves a SearchScratch (dry run gives the size).
@@ -181,7 +183,15 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
 
 // exact path: one warp per (node, projection); res holds m*P per-projection
 // results (sort_res_bytes() each), indexed by node
-cudaError_t launch_sort_warp(const SearchArgs& a, const V4* plan_total, const int32_t* tiny, const int32_t* med,
+// Split criterion of the scoring kernels.
+struct Crit {
+  int ent;            // 0: Gini decrease; 1: information gain
+  float eps;          // Gini: relative re-score window (above three times the key's relative error)
+  const double* tab;  // information gain: x ln x for x < 2048 (device), or null
+};
+
+cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan_total, const int32_t* tiny,
+                             const int32_t* med,
                              void* res, int32_t* node_cls, cudaStream_t st);
 size_t sort_res_bytes();
 

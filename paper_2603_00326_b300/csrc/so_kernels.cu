@@ -318,7 +318,7 @@ __device__ __forceinline__ void bin_prefix(const int32_t* __restrict__ H, int B,
 
 __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t P, int32_t B, int32_t C,
                                                    const int32_t* __restrict__ hist, float* max32,
-                                                   int32_t* node_counts, float* gain32_out) {
+                                                   int32_t* node_counts, float* gain32_out, Crit cr) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t
     int L[kMaxClasses];
 #pragma unroll
     for (int c = 0; c < kMaxClasses; ++c) L[c] = bp.excl[c];
-    float best = -1.0f;
+    float best = key_none(cr);
     for (int bb = 0; bb < BPL; ++bb) {
       const int b = lane * BPL + bb;
       if (b > B - 2) break;
@@ -345,8 +345,8 @@ __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t
           nL += L[c];
         }
       }
-      float g = -1.0f;
-      if (nL > 0 && nL < bp.n) g = gain32(L, bp.N, C, bp.n, nL);
+      float g = key_none(cr);
+      if (nL > 0 && nL < bp.n) g = key32(cr, L, bp.N, C, bp.n, nL);
       best = fmaxf(best, g);
       if (gain32_out) gain32_out[wi * (B - 1) + b] = g;
     }
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
                                                      const int32_t* __restrict__ hist,
                                                      const float* __restrict__ max32,
                                                      const uint32_t* __restrict__ mm,
-                                                     const float* __restrict__ rw_t, float eps,
+                                                     const float* __restrict__ rw_t, Crit cr,
                                                      so_split* out, int64_t* left_counts) {
   __shared__ float s_red[8];
   __shared__ Cand s_best[8];
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
   for (int64_t h = blockIdx.x; h < m_hist; h += gridDim.x) {
     const int j = hist_nodes[h];
     const int64_t n = off[j + 1] - off[j];
-    float m = -1.0f;
+    float m = key_none(cr);
     for (int p = threadIdx.x; p < P; p += blockDim.x) m = fmaxf(m, max32[h * P + p]);
     m = warp_max(m);
     if (lane == 0) s_red[warp] = m;
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
     float M = s_red[0];
     for (int w = 1; w < 8; ++w) M = fmaxf(M, s_red[w]);
     __syncthreads();
-    if (!(M > 0.0f)) {
+    if (!key_any(cr, M)) {
       if (threadIdx.x == 0) {
         so_split r;
         r.valid = 0; r.proj = -1; r.path = 0; r.cand = -1; r.threshold = 0.0f; r.gain = 0.0;
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
       }
       continue;
     }
-    const float thr = __fmul_rn(M, 1.0f - eps);
+    const float thr = key_thr(cr, M, n, C);
     Cand best{-1.0, INT_MAX, INT_MAX};
     for (int p = warp; p < P; p += 8) {
       if (max32[h * P + p] < thr) continue;
@@ -419,9 +419,9 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
           }
         }
         if (nL > 0 && nL < bp.n) {
-          const float g = gain32(L, bp.N, C, bp.n, nL);
+          const float g = key32(cr, L, bp.N, C, bp.n, nL);
           if (g >= thr) {
-            const Cand c{gain64(L, bp.N, C, bp.n, nL), p, b};
+            const Cand c{gain64c(cr, L, bp.N, C, bp.n, nL), p, b};
             if (better(c, best)) best = c;
           }
         }
@@ -430,7 +430,17 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
     best = warp_best(best);
     if (lane == 0) s_best[warp] = best;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !(s_best[0].g > 0.0 || s_best[1].g > 0.0 || s_best[2].g > 0.0 || s_best[3].g > 0.0 ||
+                              s_best[4].g > 0.0 || s_best[5].g > 0.0 || s_best[6].g > 0.0 || s_best[7].g > 0.0)) {
+      // no re-scored candidate with a positive double gain (information gain
+      // can round to zero or below for a split that carries almost none)
+      so_split r;
+      r.valid = 0; r.proj = -1; r.path = 0; r.cand = -1; r.threshold = 0.0f; r.gain = 0.0;
+      r.n_left = 0; r.n_right = 0;
+      out[j] = r;
+      if (left_counts)
+        for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = 0;
+    } else if (threadIdx.x == 0) {
       Cand f = s_best[0];
       for (int w = 1; w < 8; ++w)
         if (better(s_best[w], f)) f = s_best[w];
@@ -461,6 +471,13 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
     }
     __syncthreads();
   }
+}
+
+// x ln x for x < kXlnxTab, the exact path's table of the entropy criterion
+// (each entry the value xlnx64 computes, so table and direct values agree).
+__global__ void k_xlnx_table(double* tab) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < kXlnxTab) tab[x] = xlnx64(x);
 }
 
 // Copies inspection outputs of the histogram stage (slot h -> node j).
@@ -530,6 +547,7 @@ void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int3
   s.node_counts = cv.take<int32_t>((size_t)mh * C);
   s.hist = cv.take<int32_t>((size_t)mh * P * B * C);
   carve_staged(cv, s.staged, mh, P);
+  s.xlnx = cv.take<double>(kXlnxTab);
   if (bin_rule == SO_BINS_RANDOM_WIDTH) {
     s.rw.t = cv.take<float>((size_t)mh * P * kRwRow);
     s.rw.g = cv.take<uint16_t>((size_t)mh * P * kRwRow);
@@ -584,6 +602,11 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
   if (e != cudaSuccess) return e;
 
   const int grid_fill = di.num_sms * 8;
+  const Crit cr{a.criterion == SO_CRIT_ENTROPY ? 1 : 0, a.eps, a.criterion == SO_CRIT_ENTROPY ? s.xlnx : nullptr};
+  if (cr.ent) {
+    ProfScope ps_("k_xlnx_table", st);
+    k_xlnx_table<<<kXlnxTab / 256, 256, 0, st>>>(s.xlnx);
+  }
   {
     ProfScope ps_("k_hist_init", st);
     k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
@@ -618,15 +641,15 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
   }
   {
     ProfScope ps_("k_gini_scan", st);
-    k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, nullptr);
+    k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, nullptr, cr);
   }
   {
     ProfScope ps_("k_hist_select", st);
     k_hist_select<<<grid_fill, 256, 0, st>>>(s.plan_total, s.hist_nodes, a.node_off, P, B, C, s.hist, s.max32,
-                                             s.mm_keys, rw ? s.rw.t : nullptr, a.eps, a.out, a.left_counts);
+                                             s.mm_keys, rw ? s.rw.t : nullptr, cr, a.out, a.left_counts);
   }
   // exact path
-  e = launch_sort_warp(a, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls, st);
+  e = launch_sort_warp(a, cr, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -691,7 +714,8 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
   }
   {
     ProfScope ps_("k_gini_scan", st);
-    k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, gain_tmp);
+    k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, gain_tmp,
+                                           Crit{0, a.eps, nullptr});
   }
   {
     ProfScope ps_("k_hist_export", st);

@@ -46,7 +46,8 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   if (!params || params->n_bins < 2 || params->n_bins > kMaxBins || params->sort_below < 0 ||
       params->sort_below > kMaxSortBelow ||
       (params->bin_rule != SO_BINS_EQUAL_WIDTH && params->bin_rule != SO_BINS_RANDOM_WIDTH) ||
-      (params->bin_rule == SO_BINS_RANDOM_WIDTH && !params->bin_keys))
+      (params->bin_rule == SO_BINS_RANDOM_WIDTH && !params->bin_keys) ||
+      (params->criterion != SO_CRIT_GINI && params->criterion != SO_CRIT_ENTROPY))
     return noalloc_fail(SO_EINVAL, "so_split_search_noalloc: bad split parameters");
   if (!projs || projs->n_proj < 1 || projs->n_proj > kMaxProj || !projs->ptr || !projs->feat || !projs->sign ||
       projs->max_nnz < 0 || projs->max_nnz > kMaxCap)
@@ -133,6 +134,7 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   a.left_counts = lc;
   a.bin_rule = params->bin_rule;
   a.bin_keys = params->bin_keys;
+  a.criterion = params->criterion;
 
   cudaError_t e = launch_fill_off(off, n_node, cs);
   if (e == cudaSuccess) e = launch_search(a, s, cs);

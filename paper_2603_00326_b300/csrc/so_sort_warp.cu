@@ -5,16 +5,20 @@
 // the (order-preserving key, label) pairs -- one warp in registers for nodes
 // of up to kSortRegMax samples (bitonic network, lane-major layout
 // e = lane*EPL + r), one CTA in shared memory for larger exact-path nodes --
-// form class prefix counts with a packed scan, evaluate the float Gini gain of
-// every boundary between distinct values, take the projection's float
-// maximum M_p, re-score in double every candidate within M_p(1-eps) and store
-// the projection's lexicographic best (double gain, lowest position).
+// form class prefix counts with a packed scan, evaluate the float key of the
+// criterion at every boundary between distinct values, take the projection's float
+// maximum M_p, re-score in double every candidate within the criterion's
+// window below M_p (Gini: M_p(1-eps); information gain: an absolute bound
+// of the key's error) and store the projection's lexicographic best (double
+// gain, lowest position).
 // Pass 2 (k_sortw_select): one warp per node takes M = max_p M_p and the
-// lexicographic best (gain, projection, position) over the projections with
-// M_p >= M(1-eps).  The double winner of the node is always in its
-// projection's re-score set (M >= M_p), and every projection holding a
-// double tie of it has M_p >= M(1-eps) when eps exceeds three times the float
-// gain's relative error, so the result equals the double argmax.
+// lexicographic best (gain, projection, position) over the projections whose
+// M_p lies in the same window below M.  The double winner of the node is
+// always in its projection's re-score set (M >= M_p), and every projection
+// holding a double tie of it has M_p inside the window, because the window
+// exceeds twice the key's error (Gini: eps above three times its relative
+// error; information gain: three times its absolute bound), so the result
+// equals the double argmax.
 #include <climits>
 
 #include "so_device.cuh"
@@ -145,7 +149,7 @@ __device__ __forceinline__ void load_sort(const DatasetView& ds, const int32_t* 
 // positions 0..e.
 template <int EPL, class Visit>
 __device__ __forceinline__ void scan_candidates(const unsigned long long (&k)[EPL], const SortNodeCtx& nc, int C,
-                                                int lane, Visit visit) {
+                                                const Crit& cr, int lane, Visit visit) {
   PackedCnt own{0, 0};
 #pragma unroll
   for (int r = 0; r < EPL; ++r) {
@@ -176,7 +180,7 @@ __device__ __forceinline__ void scan_candidates(const unsigned long long (&k)[EP
         int L[kMaxClasses];
 #pragma unroll
         for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
-        visit(e, run, gain32(L, nc.N, C, nc.nv, e + 1), a, b);
+        visit(e, run, key32(cr, L, nc.N, C, nc.nv, e + 1), a, b);
       }
     }
   }
@@ -225,23 +229,23 @@ __device__ __forceinline__ void best_reduce(Best& lb) {
 // Both sweeps of pass 1 over an already sorted projection, through a
 // candidate walker walk(visit); writes the projection's SortRes.
 template <class Walk>
-__device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, float eps, int lane, Walk walk,
+__device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, const Crit& cr, int lane, Walk walk,
                                                  SortRes* out) {
-  float m = -1.0f;
+  float m = key_none(cr);
   walk([&](int, const PackedCnt&, float g, unsigned, unsigned) { m = fmaxf(m, g); });
   m = warp_max(m);
   Best lb;
   lb.c = Cand{-1.0, INT_MAX, INT_MAX};
   lb.ka = lb.kb = 0u;
   lb.L = PackedCnt{0, 0};
-  if (m > 0.0f) {
-    const float thr = __fmul_rn(m, 1.0f - eps);
+  if (key_any(cr, m)) {
+    const float thr = key_thr(cr, m, nc.nv, C);
     walk([&](int e, const PackedCnt& run, float g, unsigned a, unsigned b) {
       if (g >= thr) {
         int L[kMaxClasses];
 #pragma unroll
         for (int cc = 0; cc < kMaxClasses; ++cc) L[cc] = pc_get(run, cc);
-        const Cand c{gain64(L, nc.N, C, nc.nv, e + 1), 0, e};
+        const Cand c{gain64c(cr, L, nc.N, C, nc.nv, e + 1), 0, e};
         if (better(c, lb.c)) {
           lb.c = c;
           lb.ka = a;
@@ -267,22 +271,28 @@ __device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, f
 
 template <int EPL>
 __device__ __forceinline__ void proj_pass1_reg(const DatasetView& ds, const int32_t* idx, const ProjView& pv, int64_t q,
-                                               const SortNodeCtx& nc, int lane, float eps, SortRes* out) {
+                                               const SortNodeCtx& nc, int lane, const Crit& cr, SortRes* out) {
   unsigned long long k[EPL];
   load_sort<EPL>(ds, idx, pv, q, nc, lane, k);
-  score_projection(nc, ds.C, eps, lane, [&](auto visit) { scan_candidates<EPL>(k, nc, ds.C, lane, visit); }, out);
+  score_projection(nc, ds.C, cr, lane, [&](auto visit) { scan_candidates<EPL>(k, nc, ds.C, cr, lane, visit); },
+                   out);
 }
 
 __device__ __forceinline__ int epl_of(int nv) { return nv <= 32 ? 1 : nv <= 64 ? 2 : 4; }
 
 }  // namespace
 
-// Pass 1, register form: one warp per (node of <= kSortRegMax samples, projection).
+// Pass 1, register form: one warp per (node of <= kSortRegMax samples,
+// projection).  ENT fixes the criterion at compile time, so the Gini form
+// carries none of the information gain's code.
+template <int ENT>
 __global__ void __launch_bounds__(256, 4) k_sortw_scan(DatasetView ds, const int32_t* __restrict__ idx,
                                                        const int64_t* __restrict__ off, ProjView pv,
                                                        const V4* plan_total, const int32_t* nodes,
-                                                       const int32_t* __restrict__ node_cls, float eps,
+                                                       const int32_t* __restrict__ node_cls, Crit cr_in,
                                                        SortRes* res) {
+  Crit cr = cr_in;
+  cr.ent = ENT;
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -297,9 +307,9 @@ __global__ void __launch_bounds__(256, 4) k_sortw_scan(DatasetView ds, const int
     const int64_t q = (int64_t)j * P + p;
     SortRes* out = res + q;
     switch (epl_of(nc.nv)) {
-      case 1: proj_pass1_reg<1>(ds, idx, pv, q, nc, lane, eps, out); break;
-      case 2: proj_pass1_reg<2>(ds, idx, pv, q, nc, lane, eps, out); break;
-      default: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, eps, out); break;
+      case 1: proj_pass1_reg<1>(ds, idx, pv, q, nc, lane, cr, out); break;
+      case 2: proj_pass1_reg<2>(ds, idx, pv, q, nc, lane, cr, out); break;
+      default: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, cr, out); break;
     }
   }
 }
@@ -382,8 +392,8 @@ __device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP) {
 // visit(i, run, g32, a, b) for each candidate (boundary between distinct
 // values), run = packed class counts of positions 0..i.
 template <class Visit>
-__device__ __forceinline__ void sc_walk(const unsigned long long* keys, const SortNodeCtx& nc, int C, int i0, int E,
-                                        PackedCnt run, Visit visit) {
+__device__ __forceinline__ void sc_walk(const unsigned long long* keys, const SortNodeCtx& nc, int C, const Crit& cr,
+                                        int i0, int E, PackedCnt run, Visit visit) {
   for (int e = 0; e < E; ++e) {
     const int i = i0 + e;
     if (i >= nc.nv - 1) break;
@@ -394,16 +404,19 @@ __device__ __forceinline__ void sc_walk(const unsigned long long* keys, const So
       int L[kMaxClasses];
 #pragma unroll
       for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
-      visit(i, run, gain32(L, nc.N, C, nc.nv, i + 1), a, b);
+      visit(i, run, key32(cr, L, nc.N, C, nc.nv, i + 1), a, b);
     }
   }
 }
 
+template <int ENT>
 __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const int32_t* __restrict__ idx,
                                                           const int64_t* __restrict__ off, ProjView pv,
                                                           const V4* plan_total, const int32_t* nodes,
-                                                          const int32_t* __restrict__ node_cls, float eps,
+                                                          const int32_t* __restrict__ node_cls, Crit cr_in,
                                                           SortRes* res) {
+  Crit cr = cr_in;
+  cr.ent = ENT;
   extern __shared__ unsigned long long s_keys[];  // [NP <= kMaxSortBelow]
   __shared__ ScShared sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -458,8 +471,9 @@ __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const
       run.hi += sh.whi[w];
     }
     // float maximum of the projection
-    float m = -1.0f;
-    sc_walk(s_keys, nc, ds.C, i0, E, run, [&](int, const PackedCnt&, float g, unsigned, unsigned) { m = fmaxf(m, g); });
+    float m = key_none(cr);
+    sc_walk(s_keys, nc, ds.C, cr, i0, E, run,
+            [&](int, const PackedCnt&, float g, unsigned, unsigned) { m = fmaxf(m, g); });
     m = warp_max(m);
     if (lane == 0) sh.wmax[warp] = m;
     __syncthreads();
@@ -470,14 +484,14 @@ __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const
     lb.c = Cand{-1.0, INT_MAX, INT_MAX};
     lb.ka = lb.kb = 0u;
     lb.L = PackedCnt{0, 0};
-    if (m > 0.0f) {
-      const float thr = __fmul_rn(m, 1.0f - eps);
-      sc_walk(s_keys, nc, ds.C, i0, E, run, [&](int i, const PackedCnt& r, float g, unsigned a, unsigned b) {
+    if (key_any(cr, m)) {
+      const float thr = key_thr(cr, m, nc.nv, ds.C);
+      sc_walk(s_keys, nc, ds.C, cr, i0, E, run, [&](int i, const PackedCnt& r, float g, unsigned a, unsigned b) {
         if (g >= thr) {
           int L[kMaxClasses];
 #pragma unroll
           for (int cc = 0; cc < kMaxClasses; ++cc) L[cc] = pc_get(r, cc);
-          const Cand c{gain64(L, nc.N, ds.C, nc.nv, i + 1), 0, i};
+          const Cand c{gain64c(cr, L, nc.N, ds.C, nc.nv, i + 1), 0, i};
           if (better(c, lb.c)) {
             lb.c = c;
             lb.ka = a;
@@ -538,7 +552,7 @@ __global__ void __launch_bounds__(256) k_sortw_counts(DatasetView ds, const int3
 // Pass 2: one warp per exact-path node (both forms).
 __global__ void __launch_bounds__(256) k_sortw_select(const int64_t* __restrict__ off, int32_t P, int32_t C,
                                                       const V4* plan_total, const int32_t* tiny, const int32_t* med,
-                                                      const SortRes* __restrict__ res, float eps, so_split* out,
+                                                      const SortRes* __restrict__ res, Crit cr, so_split* out,
                                                       int64_t* left_counts) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -548,15 +562,15 @@ __global__ void __launch_bounds__(256) k_sortw_select(const int64_t* __restrict_
     const int j = s < m_tiny ? tiny[s] : med[s - m_tiny];
     const int nv = (int)(off[j + 1] - off[j]);
     const SortRes* rj = res + (int64_t)j * P;
-    float M = -1.0f;
+    float M = key_none(cr);
     for (int p = lane; p < P; p += 32) M = fmaxf(M, rj[p].m32);
     M = warp_max(M);
     Cand best{-1.0, INT_MAX, INT_MAX};
-    if (M > 0.0f) {
-      const float thr = __fmul_rn(M, 1.0f - eps);
+    if (key_any(cr, M)) {
+      const float thr = key_thr(cr, M, nv, C);
       for (int p = lane; p < P; p += 32) {
         const SortRes r = rj[p];
-        if (r.m32 >= thr && r.g64 >= 0.0) {
+        if (r.m32 >= thr && r.g64 > 0.0) {
           const Cand c{r.g64, p, r.cand};
           if (better(c, best)) best = c;
         }
@@ -591,8 +605,8 @@ __global__ void __launch_bounds__(256) k_sortw_select(const int64_t* __restrict_
   }
 }
 
-cudaError_t launch_sort_warp(const SearchArgs& a, const V4* plan_total, const int32_t* tiny, const int32_t* med,
-                             void* res_raw, int32_t* node_cls, cudaStream_t st) {
+cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan_total, const int32_t* tiny,
+                             const int32_t* med, void* res_raw, int32_t* node_cls, cudaStream_t st) {
   const DeviceInfo& di = device_info();
   SortRes* res = static_cast<SortRes*>(res_raw);
   {
@@ -601,20 +615,21 @@ cudaError_t launch_sort_warp(const SearchArgs& a, const V4* plan_total, const in
   }
   {
     ProfScope ps_("k_sortw_scan", st);
-    k_sortw_scan<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, tiny, node_cls, a.eps,
-                                                 res);
+    auto kern = cr.ent ? k_sortw_scan<1> : k_sortw_scan<0>;
+    kern<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, tiny, node_cls, cr, res);
   }
   if (!a.hist_only && a.T > kSortRegMax + 1) {
     int NPmax = 2 * kScThreads;
     while (NPmax < a.T - 1) NPmax <<= 1;
     const size_t smem = (size_t)NPmax * 8;
     ProfScope ps_("k_sortc_scan", st);
-    k_sortc_scan<<<di.num_sms * 16, kScThreads, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, med, node_cls,
-                                                           a.eps, res);
+    auto kern = cr.ent ? k_sortc_scan<1> : k_sortc_scan<0>;
+    kern<<<di.num_sms * 16, kScThreads, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, med, node_cls, cr,
+                                                    res);
   }
   {
     ProfScope ps_("k_sortw_select", st);
-    k_sortw_select<<<di.num_sms * 8, 256, 0, st>>>(a.node_off, a.pv.P, a.ds.C, plan_total, tiny, med, res, a.eps,
+    k_sortw_select<<<di.num_sms * 8, 256, 0, st>>>(a.node_off, a.pv.P, a.ds.C, plan_total, tiny, med, res, cr,
                                                    a.out, a.left_counts);
   }
   return cudaGetLastError();

@@ -33,6 +33,7 @@ class ForestConfig:
     bootstrap: bool = True
     max_depth: int = -1
     bin_rule: int = 0  # 0 equal-width bins, 1 random-width bins (node keys of each tree)
+    criterion: int = 0  # 0 Gini decrease, 1 information gain
 
 
 def trees_of_rank(n_trees: int, rank: int, world: int) -> List[int]:
@@ -52,7 +53,7 @@ def _gpu_trainer(ds: "S.DeviceDataset", cfg: ForestConfig):
     def train(tree_id: int) -> S.Tree:
         root = torch.from_numpy(root_indices(ds.X.shape[1], tree_id, cfg)).to(ds.X.device)
         tp = S.tree_params(cfg.n_proj, cfg.lam, cfg.cap, cfg.n_bins, cfg.sort_below, cfg.hist_only, cfg.seed,
-                           tree_id, cfg.max_depth, bin_rule=cfg.bin_rule)
+                           tree_id, cfg.max_depth, bin_rule=cfg.bin_rule, criterion=cfg.criterion)
         return S.so_train_tree(ds, root, tp)
 
     return train

@@ -10,10 +10,8 @@ and a fully re-searched tree against the plain search.  No GPU needed.
 """
 import math
 
-import mpmath
 import numpy as np
 import pytest
-from sklearn.metrics import mutual_info_score
 
 import oracle as O
 from paper_2603_00326_b300 import datagen as G
@@ -51,8 +49,13 @@ def test_xlnx_values():
         assert O.xlnx(x) == pytest.approx(x * math.log(x), rel=1e-15)
 
 
+def _mp():
+    return pytest.importorskip("mpmath")
+
+
 def _mp_gain(L, N):
     """Textbook entropy decrease H(parent) - nL/n H(L) - nR/n H(R), 40 digits."""
+    mpmath = _mp()
     mpmath.mp.dps = 40
     L = [int(c) for c in L]
     N = [int(c) for c in N]
@@ -68,6 +71,7 @@ def _mp_gain(L, N):
 
 
 def test_gain_equals_mutual_information_and_textbook():
+    mutual_info_score = pytest.importorskip("sklearn.metrics").mutual_info_score
     rng = np.random.default_rng(2)
     for _ in range(300):
         C = int(rng.integers(2, 9))
@@ -107,6 +111,7 @@ def _check(r, cands):
     """cands: (proj, cand, left set, mp gain, left counts).  The oracle's pick
     has the largest gain; where mp gains tie, the lowest (proj, cand) unless
     the double values of the tied gains order them otherwise."""
+    mpmath = _mp()
     pos = [c for c in cands if c[3] > 1e-30]
     if not pos:
         assert r.valid == 0
