@@ -388,8 +388,10 @@ def run_leg(args):
             out.update(extra_legs(S, torch, dev, 1, only="forest", rw_tree=True))
         print(json.dumps({"leg": args.leg, **out}), flush=True)
         return 0
+    # the forest leg alone grows only the equal-width Gini trees (the variant
+    # trees run in the default extras and in --leg rw)
     out = extra_legs(S, torch, dev, args.forest_trees if args.leg == "forest" else 0, only=args.leg,
-                     wide_trees=args.wide_trees if args.leg == "wide" else 0)
+                     wide_trees=args.wide_trees if args.leg == "wide" else 0, rw_tree=False)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
     return 0
 
