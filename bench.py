@@ -199,6 +199,7 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=T
                float(rec[j]["gain"]) == plain[j].gain for j in range(m))
     sp = float(ds_np.n * P)
     out["frontier_1m"] = {"nodes": m, "autotuned_sort_below": int(prm.sort_below),
+                          "autotuned_proj_per_cta": int(prm.proj_per_cta), "autotuned_chunk": int(prm.chunk),
                           "batched_ms": batched_ms, "plain_ms": plain_ms,
                           "speedup": plain_ms / batched_ms, "identical": bool(same),
                           "batched_sample_projections_per_s": sp / (batched_ms / 1000.0)}

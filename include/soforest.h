@@ -122,7 +122,13 @@ enum { SO_CRIT_GINI = 0, SO_CRIT_ENTROPY = 1 };
  *  bin_keys     SO_BINS_RANDOM_WIDTH: device uint64 [m], the key of each node
  *               of the call (node j of a batch reads bin_keys[j]; a one-node
  *               call reads bin_keys[0]); the same keys so_sample_projections
- *               takes.  Ignored (may be NULL) for equal width. */
+ *               takes.  Ignored (may be NULL) for equal width.
+ *  proj_per_cta projections whose histograms (all n_bins bins of each) one
+ *               CTA holds in shared memory per histogram work item; 0 = the
+ *               most that fit (at most 64), else 1..64 (capped at what fits).
+ *  chunk        samples per histogram work item; 0 = 16384, else
+ *               512..16384.  Neither changes any result (integer counts),
+ *               only the work decomposition; so_autotune picks both. */
 typedef struct {
     int32_t n_bins;
     int32_t sort_below;
@@ -131,6 +137,8 @@ typedef struct {
     int32_t bin_rule;
     int32_t criterion;
     const uint64_t *bin_keys;
+    int32_t proj_per_cta;
+    int32_t chunk;
 } so_split_params;
 
 /* Result of one node's split search.
@@ -268,9 +276,9 @@ so_status so_histograms(const so_dataset *ds, const int32_t *idx, int64_t n_tota
                         float *gain32_dev, float *bounds_dev, void *stream);
 
 /* Tree growth parameters.
- *  n_bins, sort_below, hist_only, rescore_rel_eps, bin_rule, criterion  as
- *             in so_split_params; random-width boundaries use the tree's node
- *             keys.
+ *  n_bins, sort_below, hist_only, rescore_rel_eps, bin_rule, criterion,
+ *             proj_per_cta, chunk  as in so_split_params; random-width
+ *             boundaries use the tree's node keys.
  *  n_proj     projections sampled per node, 1..1024.
  *  lambda, nnz_cap  nnz law of a projection: min(nnz_cap, d, 1+Poisson(lambda)).
  *  seed, tree_id    root key = splitmix64(seed ^ tree_id*0x9E3779B97F4A7C15);
@@ -289,6 +297,8 @@ typedef struct {
     int32_t max_depth;
     int32_t bin_rule;
     int32_t criterion;
+    int32_t proj_per_cta;
+    int32_t chunk;
 } so_tree_params;
 
 /* A trained tree in breadth-first order (children appended level by level in
@@ -357,8 +367,11 @@ so_status so_predict(const float *X, int64_t n, int32_t d, int64_t ld, const so_
  * drawn from ds on the exact path and on the histogram path (n_proj sampled
  * projections per node with nnz = min(nnz_cap, d, 1+Poisson(lambda))), and
  * writes into params->sort_below the smallest measured size at which the
- * histogram path is no slower per node (2048 if it never is).  Other fields
- * of params are kept.  Times per size go to times_ms_host [2*n_sizes] when
+ * histogram path is no slower per node (2048 if it never is).  Then times the
+ * histogram path of one node of min(n, 2^20) bootstrap-like samples for
+ * proj_per_cta in {16, 32, 64} (those that fit) and chunk in {4096, 8192,
+ * 16384} and writes the fastest pair into params->proj_per_cta and
+ * params->chunk.  Other fields of params are kept.  Times per size go to times_ms_host [2*n_sizes] when
  * not NULL (exact, histogram), with the sizes in sizes_host [n_sizes];
  * n_sizes_out receives the count (at most 16).  The timed searches use
  * params->n_bins and params->bin_rule (random width with keys of their own;

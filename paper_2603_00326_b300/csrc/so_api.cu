@@ -130,7 +130,17 @@ so_status check_params(const so_split_params* p, bool keys_given = true) {
     return fail(SO_EINVAL, "random-width bins need bin_keys");
   if (p->criterion != SO_CRIT_GINI && p->criterion != SO_CRIT_ENTROPY)
     return fail(SO_EINVAL, "criterion=%d is neither Gini (0) nor entropy (1)", p->criterion);
+  if (p->proj_per_cta < 0 || p->proj_per_cta > 64)
+    return fail(SO_EINVAL, "proj_per_cta=%d outside 0..64", p->proj_per_cta);
+  if (p->chunk != 0 && (p->chunk < 512 || p->chunk > 16384))
+    return fail(SO_EINVAL, "chunk=%d is neither 0 nor in 512..16384", p->chunk);
   return SO_OK;
+}
+
+// The histogram work decomposition a caller (or so_autotune) chose.
+void apply_tuning(SearchArgs& a, int32_t proj_per_cta, int32_t chunk) {
+  a.tune.staged_pg = proj_per_cta;
+  if (chunk > 0) a.tune.chunk = chunk;
 }
 
 so_status check_projs(const so_projs* pr) {
@@ -303,6 +313,7 @@ so_status so_split_search_batch(const so_dataset* ds, const int32_t* idx, int64_
     a.bin_rule = params->bin_rule;
     a.bin_keys = params->bin_keys;
     a.criterion = params->criterion;
+    apply_tuning(a, params->proj_per_cta, params->chunk);
     SO_CK(launch_search(a, s, cs));
     return SO_OK;
   });
@@ -359,6 +370,7 @@ so_status so_split_search(const so_dataset* ds, const int32_t* idx, int64_t n_no
     a.bin_rule = params->bin_rule;
     a.bin_keys = params->bin_keys;
     a.criterion = params->criterion;
+    apply_tuning(a, params->proj_per_cta, params->chunk);
     SO_CK(launch_search(a, s, cs));
     int64_t lch[kMaxClasses];
     SO_CK(cudaMemcpyAsync(out_host, out_dev, sizeof(so_split), cudaMemcpyDeviceToHost, cs));
@@ -572,7 +584,8 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
     if (n_root < 1 || n_root > INT32_MAX / 2) return fail(SO_EINVAL, "n_root out of range");
     if (!root_idx) return fail(SO_EINVAL, "root_idx is NULL");
     so_split_params sp{tp->n_bins,   tp->sort_below, tp->hist_only, tp->rescore_rel_eps,
-                       tp->bin_rule, tp->criterion,  nullptr};
+                       tp->bin_rule, tp->criterion,  nullptr,       tp->proj_per_cta,
+                       tp->chunk};
     if ((st = check_params(&sp, false))) return st;
     if (tp->n_proj < 1 || tp->n_proj > kMaxProj) return fail(SO_EINVAL, "n_proj outside 1..1024");
     if (tp->nnz_cap < 1 || tp->nnz_cap > kMaxCap) return fail(SO_EINVAL, "nnz_cap outside 1..32");
@@ -736,6 +749,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
           a.bin_rule = tp->bin_rule;
           a.bin_keys = cur.key + j0;  // random-width boundaries from the node keys
           a.criterion = tp->criterion;
+          apply_tuning(a, tp->proj_per_cta, tp->chunk);
           e = launch_search(a, ss, ls);
           if (e == cudaSuccess)
             e = launch_tree_record_splits((int32_t)j0, mb, cur, spl, snnz, sfeat, ssign, P, cap, td, ls);
@@ -965,10 +979,58 @@ so_status so_autotune(const so_dataset* ds, int32_t n_proj, double lambda, int32
         found = 1;
       }
     }
+    // histogram work decomposition: one node of up to 2^20 sorted random
+    // draws (a bootstrap-like root), histogram path, for each projections-
+    // per-CTA and chunk candidate; the fastest pair is kept
+    int best_pg = 0, best_chunk = 0;
+    {
+      const int32_t nh = (int32_t)std::min<int64_t>(std::min<int64_t>(ds->n, (int64_t)1 << 20), ncap);
+      SO_CK(launch_bench_nodes(1, nh, ds->n, 0x5EED7ull, idx, off, keys, cs));
+      SO_CK(launch_sample(1, keys, P, ds->d, lambda, cap, snnz, sfeat, ssign, sbeg, send, cs));
+      const bool rw = params->bin_rule == SO_BINS_RANDOM_WIDTH;
+      const int pg_max = staged_supported(ds->d) ? hist_group_size(B, C, rw) : 0;
+      float best_ms = 0.0f;
+      for (int pg : {16, 32, 64}) {
+        if (pg_max == 0 ? pg != 16 : pg > pg_max) continue;  // general kernels: the chunk alone
+        for (int ch : {4096, 8192, 16384}) {
+          SearchArgs a;
+          a.ds = view_of(ds);
+          a.idx = idx;
+          a.n_total = nh;
+          a.node_off = off;
+          a.m = 1;
+          a.pv = ProjView{sbeg, send, sfeat, ssign, P};
+          a.B = B;
+          a.T = 0;
+          a.hist_only = 1;
+          a.eps = effective_eps(params->rescore_rel_eps, C);
+          a.max_nnz = cap;
+          a.out = out;
+          a.bin_rule = params->bin_rule;
+          a.bin_keys = keys;
+          a.criterion = params->criterion;
+          apply_tuning(a, pg_max == 0 ? 0 : pg, ch);
+          SO_CK(launch_search(a, ss, cs));  // warm-up
+          SO_CK(cudaEventRecord(e0, cs));
+          for (int r = 0; r < 3; ++r) SO_CK(launch_search(a, ss, cs));
+          SO_CK(cudaEventRecord(e1, cs));
+          SO_CK(cudaEventSynchronize(e1));
+          float ms = 0.0f;
+          SO_CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (best_chunk == 0 || ms < best_ms) {
+            best_ms = ms;
+            best_pg = pg_max == 0 ? 0 : pg;
+            best_chunk = ch;
+          }
+        }
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (n_sizes_out) *n_sizes_out = n_sizes;
     params->sort_below = best;
+    params->proj_per_cta = best_pg;
+    params->chunk = best_chunk;
     return SO_OK;
   });
 }

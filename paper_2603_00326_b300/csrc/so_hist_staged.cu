@@ -1257,7 +1257,8 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
   const DeviceInfo& di = device_info();
   const int C = a.ds.C, B = a.B, d = a.ds.d;
   const bool RW = a.bin_rule == SO_BINS_RANDOM_WIDTH;
-  const int PG = hist_group_size(B, C, RW);
+  int PG = hist_group_size(B, C, RW);
+  if (a.tune.staged_pg > 0 && a.tune.staged_pg < PG) PG = a.tune.staged_pg;
   // histogram items: at most kMaxItem samples (label bytes in shared memory,
   // 16-bit counters); min / max items a quarter of that, so that a single
   // large node still spreads over every SM

@@ -66,7 +66,8 @@ struct Carver {
 // change them).
 struct HistTuning {
   int32_t chunk = 16384;  // samples per work item (S)
-  int32_t pgroup = 8;     // projections per work item (one warp each)
+  int32_t pgroup = 8;     // projections per work item of the general kernels (one warp each)
+  int32_t staged_pg = 0;  // projections per work item of the staged kernels (0: the most that fit)
 };
 
 // Random-width boundary tables of the histogram nodes (one row of kRwRow per
@@ -197,6 +198,7 @@ size_t sort_res_bytes();
 
 // staged-tile histogram path (features up to 65536)
 bool staged_supported(int d);
+int hist_group_size(int B, int C, bool rw);  // the most projections per staged histogram item
 void carve_staged(Carver& cv, StagedScratch& s, int64_t m_hist_cap, int P);
 cudaError_t launch_staged(const SearchArgs& a, const V4* plan_total, const int32_t* hist_nodes,
                           int64_t m_hist_cap, const StagedScratch& ss, uint32_t* mm, int32_t* hist,

@@ -47,7 +47,8 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
       params->sort_below > kMaxSortBelow ||
       (params->bin_rule != SO_BINS_EQUAL_WIDTH && params->bin_rule != SO_BINS_RANDOM_WIDTH) ||
       (params->bin_rule == SO_BINS_RANDOM_WIDTH && !params->bin_keys) ||
-      (params->criterion != SO_CRIT_GINI && params->criterion != SO_CRIT_ENTROPY))
+      (params->criterion != SO_CRIT_GINI && params->criterion != SO_CRIT_ENTROPY) || params->proj_per_cta < 0 ||
+      params->proj_per_cta > 64 || (params->chunk != 0 && (params->chunk < 512 || params->chunk > 16384)))
     return noalloc_fail(SO_EINVAL, "so_split_search_noalloc: bad split parameters");
   if (!projs || projs->n_proj < 1 || projs->n_proj > kMaxProj || !projs->ptr || !projs->feat || !projs->sign ||
       projs->max_nnz < 0 || projs->max_nnz > kMaxCap)
@@ -135,6 +136,8 @@ extern "C" so_status so_split_search_noalloc(const so_dataset* ds, const int32_t
   a.bin_rule = params->bin_rule;
   a.bin_keys = params->bin_keys;
   a.criterion = params->criterion;
+  a.tune.staged_pg = params->proj_per_cta;
+  if (params->chunk > 0) a.tune.chunk = params->chunk;
 
   cudaError_t e = launch_fill_off(off, n_node, cs);
   if (e == cudaSuccess) e = launch_search(a, s, cs);

@@ -45,7 +45,7 @@ SO_CRIT_ENTROPY = 1
 class so_split_params(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("sort_below", C.c_int32), ("hist_only", C.c_int32),
                 ("rescore_rel_eps", C.c_float), ("bin_rule", C.c_int32), ("criterion", C.c_int32),
-                ("bin_keys", C.c_void_p)]
+                ("bin_keys", C.c_void_p), ("proj_per_cta", C.c_int32), ("chunk", C.c_int32)]
 
 
 class so_split(C.Structure):
@@ -58,7 +58,8 @@ class so_tree_params(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("sort_below", C.c_int32), ("hist_only", C.c_int32),
                 ("rescore_rel_eps", C.c_float), ("n_proj", C.c_int32), ("lambda_", C.c_double),
                 ("nnz_cap", C.c_int32), ("seed", C.c_uint64), ("tree_id", C.c_int32),
-                ("max_depth", C.c_int32), ("bin_rule", C.c_int32), ("criterion", C.c_int32)]
+                ("max_depth", C.c_int32), ("bin_rule", C.c_int32), ("criterion", C.c_int32),
+                ("proj_per_cta", C.c_int32), ("chunk", C.c_int32)]
 
 
 class so_tree(C.Structure):
@@ -201,12 +202,13 @@ class DeviceProjs:
 
 
 def split_params(n_bins=256, sort_below=1024, hist_only=False, rescore_rel_eps=0.0, bin_rule=0,
-                 bin_keys=None, criterion=0) -> so_split_params:
+                 bin_keys=None, criterion=0, proj_per_cta=0, chunk=0) -> so_split_params:
     """bin_rule SO_BINS_RANDOM_WIDTH needs bin_keys: a device int64 tensor [m]
     holding the nodes' uint64 keys (kept alive by the returned struct).
-    criterion SO_CRIT_GINI or SO_CRIT_ENTROPY."""
+    criterion SO_CRIT_GINI or SO_CRIT_ENTROPY.  proj_per_cta, chunk: the
+    histogram work decomposition (0: defaults; so_autotune picks them)."""
     p = so_split_params(n_bins, sort_below, 1 if hist_only else 0, rescore_rel_eps, bin_rule, criterion,
-                        _ptr(bin_keys))
+                        _ptr(bin_keys), proj_per_cta, chunk)
     p._keys = bin_keys
     return p
 
@@ -365,9 +367,11 @@ class Tree:
 
 
 def tree_params(n_proj, lam, cap, n_bins=256, sort_below=1024, hist_only=False, seed=0, tree_id=0,
-                max_depth=-1, rescore_rel_eps=0.0, bin_rule=0, criterion=0) -> so_tree_params:
+                max_depth=-1, rescore_rel_eps=0.0, bin_rule=0, criterion=0, proj_per_cta=0,
+                chunk=0) -> so_tree_params:
     return so_tree_params(n_bins, sort_below, 1 if hist_only else 0, rescore_rel_eps, n_proj, lam, cap,
-                          seed & 0xFFFFFFFFFFFFFFFF, tree_id, max_depth, bin_rule, criterion)
+                          seed & 0xFFFFFFFFFFFFFFFF, tree_id, max_depth, bin_rule, criterion, proj_per_cta,
+                          chunk)
 
 
 def so_train_tree(ds: DeviceDataset, root_idx, params: so_tree_params, stream=None) -> Tree:

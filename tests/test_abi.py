@@ -64,7 +64,10 @@ def test_bad_dataset_rejected_on_host(L, kw, what):
     assert what in S.so_last_error()
 
 
-@pytest.mark.parametrize("prm", [dict(n_bins=1), dict(n_bins=257), dict(sort_below=-1), dict(sort_below=5000)])
+@pytest.mark.parametrize("prm", [dict(n_bins=1), dict(n_bins=257), dict(sort_below=-1), dict(sort_below=5000),
+                                 dict(bin_rule=2), dict(bin_rule=1), dict(criterion=2), dict(criterion=-1),
+                                 dict(proj_per_cta=-1), dict(proj_per_cta=65), dict(chunk=100),
+                                 dict(chunk=20000)])
 def test_bad_params_rejected_on_host(L, prm):
     from paper_2603_00326_b300 import soforest as S
     ds = _fake_dataset()
@@ -132,3 +135,38 @@ def test_predict_argument_checks(L):
     assert L.so_predict(None, 0, 4, 0, C.byref(f3), None, None, None) == S.SO_EINVAL
     # an empty forest over zero samples is a no-op
     assert L.so_predict(None, 0, 4, 0, C.byref(f3), None, C.byref(pred), None) == S.SO_OK
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ABI struct of the binding has the C header's size and field
+    offsets (compiled here with the host C compiler)."""
+    import os
+    import shutil
+    import subprocess
+    from paper_2603_00326_b300 import soforest as S
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = {"so_dataset": S.so_dataset, "so_projs": S.so_projs, "so_split_params": S.so_split_params,
+               "so_split": S.so_split, "so_tree_params": S.so_tree_params, "so_tree": S.so_tree,
+               "so_forest": S.so_forest, "so_profile_entry": S.so_profile_entry}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", "#include \"soforest.h\"", "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            cname = "lambda" if fname == "lambda_" else fname
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {cname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)

@@ -434,3 +434,48 @@ def test_forest_bootstrap_trees_match_oracle(S, row_major):
         ot = O.train_tree(ds_np.X, ds_np.y, 2, root, n_proj=16, lam=1.5, cap=8, sort_below=512, seed=cfg.seed,
                           tree_id=t)
         U.assert_tree_equal(gt, ot)
+
+
+# ---------------------------------------------------------------- work decomposition
+
+@pytest.mark.parametrize("ppc,chunk", [(1, 512), (2, 1000), (7, 4096), (16, 2048), (32, 16384), (64, 8192)])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_decomposition_knobs_leave_results_unchanged(S, ppc, chunk, rule):
+    """Projections per CTA and samples per histogram item change only the work
+    decomposition: histograms and splits stay the oracle's."""
+    rng = np.random.default_rng(ppc * 31 + chunk + rule)
+    n, d, P, C = 50000, 24, 40, 3
+    X = rng.standard_normal((d, n)).astype(np.float32)
+    y = rng.integers(0, C, n).astype(np.uint8)
+    sizes = [30001, 7777, 1500]
+    idx, off = _mixed_nodes(rng, n, sizes)
+    projs = [G.random_projections(rng, P, d, 1.5, 8) for _ in sizes]
+    ptr, feat, sign = U.concat_projs([(q.ptr, q.feat, q.sign) for q in projs])
+    keys = rng.integers(0, 2 ** 62, len(sizes), dtype=np.int64)
+    kt = U.i64(keys) if rule else None
+    ds = U.upload_dataset(X, y, C)
+    pj = U.upload_projs(ptr, feat, sign, P)
+    prm = S.split_params(256, 1024, True, bin_rule=rule, bin_keys=kt, proj_per_cta=ppc, chunk=chunk)
+    out, lc = S.so_split_search_batch(ds, U.i32(idx), U.i64(off), pj, prm)
+    rec = S.splits_to_numpy(out)
+    for j in range(len(sizes)):
+        nptr, nf, ns = U.oracle_node_projs(ptr, feat, sign, P, j)
+        r = O.split_search(X, y, C, idx[off[j]:off[j + 1]], nptr, nf, ns, hist_only=True, bin_rule=rule,
+                           bin_key=int(keys[j]))
+        U.assert_split_equal(rec[j], r, f"node {j} ppc {ppc} chunk {chunk}")
+    one, _ = S.so_split_search(ds, U.i32(idx[:sizes[0]]), U.upload_projs(*U.oracle_node_projs(ptr, feat, sign, P, 0),
+                                                                         P), prm)
+    U.assert_split_equal(one, O.split_search(X, y, C, idx[:sizes[0]], *U.oracle_node_projs(ptr, feat, sign, P, 0),
+                                             hist_only=True, bin_rule=rule, bin_key=int(keys[0])))
+
+
+def test_autotuned_decomposition_and_tree(S):
+    ds_np = G.tree_small(n=20000, d=16, seed=58)
+    ds = U.upload_dataset(ds_np.X, ds_np.y, 2)
+    prm, _, _ = S.so_autotune(ds, 16, 1.5, 8, S.split_params(256, 1024, False))
+    assert prm.proj_per_cta in (16, 32, 64) and prm.chunk in (4096, 8192, 16384)
+    tp = S.tree_params(16, 1.5, 8, 256, prm.sort_below, seed=3, proj_per_cta=prm.proj_per_cta, chunk=prm.chunk)
+    gt = S.so_train_tree(ds, U.i32(G.all_indices(ds_np.n)), tp)
+    ot = O.train_tree(ds_np.X, ds_np.y, 2, G.all_indices(ds_np.n), n_proj=16, lam=1.5, cap=8,
+                      sort_below=prm.sort_below, seed=3)
+    U.assert_tree_equal(gt, ot)
