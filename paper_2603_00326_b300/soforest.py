@@ -455,6 +455,43 @@ def so_predict(X, forest: DeviceForest, want_votes: bool = False, stream=None):
     return pred, votes
 
 
+def _autotune_key(ds, n_proj, lam, cap, params, gpu: str) -> str:
+    return (f"{gpu}|n={ds.X.shape[1]}|d={ds.X.shape[0]}|C={ds.n_classes}|P={n_proj}|lam={lam}|cap={cap}"
+            f"|B={params.n_bins}|rule={params.bin_rule}|crit={params.criterion}|rowmajor={int(ds.Xr is not None)}")
+
+
+def autotune_cached(ds: DeviceDataset, n_proj: int, lam: float, cap: int, params: so_split_params,
+                    cache_path=None, stream=None):
+    """so_autotune with its choices (crossover T, projections per CTA, samples
+    per item) cached as JSON per GPU model and workload shape; a later call
+    with the same key reuses them without timing.  Returns (params, cached)."""
+    import json
+    import os
+    import torch
+    path = cache_path or os.path.join(os.path.expanduser("~"), ".cache", "soforest", "autotune.json")
+    dev = ds.X.device
+    gpu = torch.cuda.get_device_name(dev) if dev.type == "cuda" else str(dev)
+    key = _autotune_key(ds, n_proj, lam, cap, params, gpu)
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+    except (OSError, ValueError):
+        table = {}
+    hit = table.get(key)
+    if hit is not None:
+        params.sort_below, params.proj_per_cta, params.chunk = hit["sort_below"], hit["proj_per_cta"], hit["chunk"]
+        return params, True
+    params, _, _ = so_autotune(ds, n_proj, lam, cap, params, stream)
+    table[key] = {"sort_below": int(params.sort_below), "proj_per_cta": int(params.proj_per_cta),
+                  "chunk": int(params.chunk)}
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(table, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return params, False
+
+
 def so_autotune(ds: DeviceDataset, n_proj: int, lam: float, cap: int, params: so_split_params, stream=None):
     """Crossover microbenchmark; sets params.sort_below.  Returns (params, sizes, times_ms[n,2])."""
     d = ds.c()
