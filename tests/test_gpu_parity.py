@@ -314,7 +314,6 @@ def test_tree_parity_tree_small_full(S):
 @pytest.mark.parametrize("variant", ["multiclass_bootstrap", "hist_only_b32", "max_depth", "counts_ties",
                                      "tiny_T", "trunk"])
 def test_tree_parity_variants(S, variant):
-    rng = np.random.default_rng(hash(variant) % 1000)
     if variant == "multiclass_bootstrap":
         ds = G.root_4m(n=6000, d=20, seed=99)
         root = G.bootstrap_indices(ds.n, 3, seed=7)
