@@ -248,19 +248,26 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
         torch.cuda.synchronize()
         pred_s = time.perf_counter() - t0
         oob_acc = []
+        votes = torch.zeros((fs.n, 2), dtype=torch.int32, device=dev)  # out-of-bag votes per sample
         for t, tr in enumerate(trees):
             inbag = np.zeros(fs.n, bool)
             inbag[F.root_indices(fs.n, t, cfg)] = True
             p1, _ = S.so_predict(dd.X, S.upload_forest([tr], 2))
             oob = ~inbag
             oob_acc.append(float((p1.cpu().numpy()[oob] == fs.y[oob]).mean()))
+            ob = torch.from_numpy(np.flatnonzero(oob)).to(dev)
+            votes[ob, p1[ob].long()] += 1
+        has = votes.sum(1) > 0
+        ens = (votes.argmax(1).to(torch.uint8) == torch.from_numpy(fs.y).to(dev)) & has
+        oob_ensemble = float(ens.sum().item() / max(int(has.sum().item()), 1))
         out["forest_2m"] = {"trees": forest_trees, "of": fp["n_trees"], "train_s": secs,
                             "s_per_tree": secs / forest_trees,
                             "projected_forest_s": secs / forest_trees * fp["n_trees"],
                             "mean_nodes": float(np.mean([t.n_nodes for t in trees])),
                             "max_depth": int(max(int(t.depth.max()) for t in trees)),
                             "predict_sample_trees_per_s": fs.n * forest_trees / pred_s,
-                            "oob_accuracy_per_tree": oob_acc}
+                            "oob_accuracy_per_tree": oob_acc[:8], "oob_accuracy_mean": float(np.mean(oob_acc)),
+                            "oob_ensemble_accuracy": oob_ensemble}
         if rw_tree:
             # tree 0 again with random-width bins (the YDF default of the
             # paper's Section 1 footnote): time and out-of-bag accuracy

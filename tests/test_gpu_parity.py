@@ -478,3 +478,23 @@ def test_autotuned_decomposition_and_tree(S):
     ot = O.train_tree(ds_np.X, ds_np.y, 2, G.all_indices(ds_np.n), n_proj=16, lam=1.5, cap=8,
                       sort_below=prm.sort_below, seed=3)
     U.assert_tree_equal(gt, ot)
+
+
+def test_forest_training_is_deterministic(S):
+    """The same forest trained twice gives identical tree arrays (every field,
+    every tree), hashed."""
+    import hashlib
+    from paper_2603_00326_b300 import forest as F
+    ds_np = G.forest_2m(n=20000, d=32, seed=88)
+    ds = U.upload_dataset(ds_np.X, ds_np.y, 2).with_row_major()
+    cfg = F.ForestConfig(n_trees=3, n_proj=16, lam=1.5, cap=8, sort_below=512)
+
+    def digest(trees):
+        h = hashlib.sha256()
+        for t in trees:
+            for f in S.Tree.FIELDS:
+                h.update(np.ascontiguousarray(getattr(t, f)).tobytes())
+        return h.hexdigest()
+    a, _ = F.train_forest(cfg, ds)
+    b, _ = F.train_forest(cfg, ds)
+    assert digest(a) == digest(b)
