@@ -418,11 +418,14 @@ __device__ __forceinline__ int choose_st_pad(int U) {
 __global__ void __launch_bounds__(128) k_groups(const V4* plan_total, const int32_t* hist_nodes, ProjView pv, int d,
                                                 int umax1, int pmax1, int umax2, int pmax2, int32_t* ng1,
                                                 int32_t* gs1, int32_t* ng2, int32_t* gs2) {
-  extern __shared__ uint32_t s_grp[];  // per warp: bitmap [nw] + set-word list [kStUMax]
+  // per warp: bitmap [nw], set-word list [kStUMax], and the features of 32
+  // projection rows [32][32] (lane l holds feature l of each row)
+  extern __shared__ uint32_t s_grp[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (d + 31) >> 5;
-  uint32_t* bits = s_grp + warp * (nw + kStUMax);
+  uint32_t* bits = s_grp + warp * (nw + kStUMax + 32 * 33);
   uint32_t* setw = bits + nw;
+  int* rowf = reinterpret_cast<int*>(setw + kStUMax);  // [32][33]: padded against bank conflicts
   for (int w = lane; w < nw; w += 32) bits[w] = 0u;
   __syncwarp();
   const int64_t m_hist = plan_total->x;
@@ -444,15 +447,58 @@ __global__ void __launch_bounds__(128) k_groups(const V4* plan_total, const int3
       }
       int U = 0, cnt = 0, nset = 0, g = 0;
       if (lane == 0) gs[0] = 0;
+      int k_l = 0;  // lane l: length of row p0 + l
+      // d <= 1024: the group's feature bitmap in registers, lane l holding
+      // features 32l .. 32l+31 (a bit test is one shuffle, no atomics)
+      const bool regmap = d <= 1024;
+      uint32_t word = 0u;
       for (int p = 0; p < P; ++p) {
-        const int64_t q = j * P + p;
-        const int rb = pv.beg[q];
-        int k = pv.end[q] - rb;
-        k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
-        int f = 0;
-        if (lane < k) {
-          f = pv.feat[rb + lane];
-          f = (f < 0 || f >= d) ? 0 : f;
+        if ((p & 31) == 0) {
+          // rows p .. p+31 at once: their bounds in one load, then all their
+          // features with the loads in flight together
+          int rb_l = 0;
+          k_l = 0;
+          if (p + lane < P) {
+            const int64_t q = j * P + p + lane;
+            rb_l = pv.beg[q];
+            const int kk = pv.end[q] - rb_l;
+            k_l = kk < 0 ? 0 : (kk > kMaxCap ? kMaxCap : kk);
+          }
+          __syncwarp();  // the previous rows' features are no longer read
+#pragma unroll 8
+          for (int pp = 0; pp < 32; ++pp) {
+            const int rb = __shfl_sync(0xffffffffu, rb_l, pp);
+            const int kk = __shfl_sync(0xffffffffu, k_l, pp);
+            int f = 0;
+            if (lane < kk) {
+              f = pv.feat[rb + lane];
+              f = (f < 0 || f >= d) ? 0 : f;
+            }
+            rowf[pp * 33 + lane] = f;
+          }
+          __syncwarp();
+        }
+        const int k = __shfl_sync(0xffffffffu, k_l, p & 31);
+        const int f = rowf[(p & 31) * 33 + lane];
+        if (regmap) {
+          const uint32_t ow = __shfl_sync(0xffffffffu, word, (f >> 5) & 31);
+          bool fresh = lane < k && !((ow >> (f & 31)) & 1u);
+          int add = __popc(__ballot_sync(0xffffffffu, fresh));
+          if (cnt > 0 && (U + add > umax || cnt + 1 > pmax)) {
+            word = 0u;
+            U = 0;
+            cnt = 0;
+            ++g;
+            if (lane == 0) gs[g] = p;
+            add = __popc(__ballot_sync(0xffffffffu, lane < k));
+          }
+          for (int jj = 0; jj < k; ++jj) {  // each feature of the row to its owner lane
+            const int fj = __shfl_sync(0xffffffffu, f, jj);
+            if ((fj >> 5) == lane) word |= 1u << (fj & 31);
+          }
+          U += add;
+          ++cnt;
+          continue;
         }
         bool fresh = lane < k && !(bits[f >> 5] & (1u << (f & 31)));
         int add = __popc(__ballot_sync(0xffffffffu, fresh));
@@ -1266,7 +1312,7 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
   const int64_t S1 = S2 / 4 > 1024 ? S2 / 4 : (S2 < 1024 ? S2 : 1024);
   cudaError_t e;
   {
-    const size_t smem = (size_t)4 * (((d + 31) >> 5) + kStUMax) * 4;
+    const size_t smem = (size_t)4 * (((d + 31) >> 5) + kStUMax + 32 * 33) * 4;
     if (smem > 48 * 1024) {
       e = cudaFuncSetAttribute(k_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;

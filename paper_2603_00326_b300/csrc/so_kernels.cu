@@ -405,8 +405,12 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
       BinPrefix bp;
       bin_prefix(H, B, C, lane, BPL, bp);
       int L[kMaxClasses];
+      long long prev_nL = 0;  // left size of the candidate before this lane's first
 #pragma unroll
-      for (int c = 0; c < kMaxClasses; ++c) L[c] = bp.excl[c];
+      for (int c = 0; c < kMaxClasses; ++c) {
+        L[c] = bp.excl[c];
+        if (c < C) prev_nL += L[c];
+      }
       for (int bb = 0; bb < BPL; ++bb) {
         const int b = lane * BPL + bb;
         if (b > B - 2) break;
@@ -418,7 +422,11 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
             nL += L[c];
           }
         }
-        if (nL > 0 && nL < bp.n) {
+        // an empty bin b repeats candidate b-1's partition (same double gain
+        // bits, lower index), so it can never be the lexicographic argmax
+        const bool repeat = b > 0 && nL == prev_nL;
+        prev_nL = nL;
+        if (!repeat && nL > 0 && nL < bp.n) {
           const float g = key32(cr, L, bp.N, C, bp.n, nL);
           if (g >= thr) {
             const Cand c{gain64c(cr, L, bp.N, C, bp.n, nL), p, b};
