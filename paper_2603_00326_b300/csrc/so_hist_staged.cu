@@ -1303,8 +1303,24 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
   const DeviceInfo& di = device_info();
   const int C = a.ds.C, B = a.B, d = a.ds.d;
   const bool RW = a.bin_rule == SO_BINS_RANDOM_WIDTH;
+  auto kern = RW ? k_hist_staged<KMAX, true> : k_hist_staged<KMAX, false>;
   int PG = hist_group_size(B, C, RW);
   if (a.tune.staged_pg > 0 && a.tune.staged_pg < PG) PG = a.tune.staged_pg;
+  {
+    // the group's counters, tables and the fixed regions (which grow with
+    // the row width KMAX) must fit one CTA's shared memory with the
+    // kernel's static shared memory
+    static thread_local size_t static_bytes[2] = {0, 0};
+    static thread_local bool have[2] = {false, false};
+    if (!have[RW]) {
+      cudaFuncAttributes fa{};
+      if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return cudaGetLastError();
+      static_bytes[RW] = fa.sharedSizeBytes;
+      have[RW] = true;
+    }
+    while (PG > 1 && hist_smem_bytes(d, KMAX, B, C, PG, RW) + static_bytes[RW] > (size_t)di.smem_optin)
+      PG = PG > kStWarps ? kStWarps : PG - 1;
+  }
   // histogram items: at most kMaxItem samples (label bytes in shared memory,
   // 16-bit counters); min / max items a quarter of that, so that a single
   // large node still spreads over every SM
@@ -1339,7 +1355,6 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
   }
   {
     const size_t smem = hist_smem_bytes(d, KMAX, B, C, PG, RW);
-    auto kern = RW ? k_hist_staged<KMAX, true> : k_hist_staged<KMAX, false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ProfScope ps_("k_hist", st);

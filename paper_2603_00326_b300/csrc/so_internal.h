@@ -177,6 +177,7 @@ class ProfScope {
 struct DeviceInfo {
   int device = 0;
   int num_sms = 148;
+  int smem_optin = 232448;  // largest shared memory of one CTA (static + dynamic), bytes
 };
 const DeviceInfo& device_info();
 

@@ -40,6 +40,9 @@ const DeviceInfo& device_info() {
     info.device = dev;
     int sms = 148;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) info.num_sms = sms;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && optin > 0)
+      info.smem_optin = optin;
     cached = dev;
   }
   return info;
