@@ -553,9 +553,10 @@ def run_ours(args):
     rec = S.SPLIT_DTYPE and np.frombuffer(out_h.numpy().tobytes(), dtype=S.SPLIT_DTYPE)[0]
 
     # ---- roofline of the dominant kernel (histogram fill)
-    # DRAM bytes (read + write) of one k_hist_staged launch on this workload, from the ncu capture
-    # summarised in profiles/k_hist_staged_root_4m.md; set to None whenever that kernel changes.
-    K_HIST_TRAFFIC_BYTES = 1_100_073_000 + 7_715_840
+    # DRAM bytes (read + write) of one k_hist_staged launch on this workload, the mean of five
+    # launches in the ncu capture summarised in profiles/kernels_dram_root_4m.md; set to None
+    # whenever that kernel changes.
+    K_HIST_TRAFFIC_BYTES = 1_099_972_556 + 4_253_491
     hbm, peak_kind = peaks()
     used_feats = np.unique(pr.feat).size
     alg_bytes = used_feats * n * 4 + n * 4 + n * 1  # feature columns + index list + labels, one pass
