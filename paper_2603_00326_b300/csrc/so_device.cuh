@@ -265,6 +265,26 @@ __device__ __forceinline__ float ent_key32(const int* L, const int* N, int C, in
     if (c < C) s = __fadd_rn(__fadd_rn(s, xlg2x(L[c])), xlg2x((long long)N[c] - L[c]));
   return __fsub_rn(__fsub_rn(s, xlg2x(nL)), xlg2x(n - nL));
 }
+// The same key for exact-path nodes (n < 2048, so every product n L_c fits
+// 32 bits and every count converts to float exactly): the same bits with
+// 32-bit arithmetic.
+__device__ __forceinline__ float xlg2x_i(int x) {
+  const float xf = __int2float_rn(x);
+  return x < 2 ? 0.0f : __fmul_rn(xf, __log2f(xf));
+}
+__device__ __forceinline__ float ent_key32_small(const int* L, const int* N, int C, int n, int nL) {
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) any |= n * L[c] != N[c] * nL;
+  if (!any) return -INFINITY;
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) s = __fadd_rn(__fadd_rn(s, xlg2x_i(L[c])), xlg2x_i(N[c] - L[c]));
+  return __fsub_rn(__fsub_rn(s, xlg2x_i(nL)), xlg2x_i(n - nL));
+}
+
 // Re-score window of the key at a node of n samples: every candidate's key
 // is within E of its double gain (same units), with m = 2C+2 terms of size at
 // most F = n log2 n (all terms sum to at most 2F), per-term error 2^-21
@@ -282,6 +302,60 @@ __device__ __forceinline__ float ent_window(int64_t n, int C) {
 // double gain.
 __device__ __forceinline__ float key32(const Crit& cr, const int* L, const int* N, int C, int64_t n, int64_t nL) {
   return cr.ent ? ent_key32(L, N, C, n, nL) : gain32(L, N, C, n, nL);
+}
+// exact-path nodes (fewer than 2048 samples): every count is in the table
+// of x ln x, so the double gain needs no logarithm (the same bits)
+__device__ __forceinline__ double ent_gain64_small(const int* L, const int* N, int C, int n, int nL,
+                                                   const double* __restrict__ tab) {
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) any |= n * L[c] != N[c] * nL;
+  if (!any) return 0.0;
+  double t = tab[n];
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) t = __dsub_rn(t, tab[N[c]]);
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) t = __dadd_rn(t, tab[L[c]]);
+  t = __dsub_rn(t, tab[nL]);
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c)
+    if (c < C) t = __dadd_rn(t, tab[N[c] - L[c]]);
+  t = __dsub_rn(t, tab[n - nL]);
+  return __ddiv_rn(t, __int2double_rn(n));
+}
+// Gini key and gain of exact-path nodes: |D_c| < n^2 < 2^22 fits 32 bits and
+// converts exactly, so these are gain32 / gain64 bit for bit
+__device__ __forceinline__ float gain32_small(const int* L, const int* N, int C, int n, int nL) {
+  float num = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) {
+    if (c < C) {
+      const float fd = __int2float_rn(n * L[c] - N[c] * nL);
+      num = __fadd_rn(num, __fmul_rn(fd, fd));
+    }
+  }
+  return __fdiv_rn(num, __fmul_rn(__int2float_rn(nL), __int2float_rn(n - nL)));
+}
+__device__ __forceinline__ double gain64_small(const int* L, const int* N, int C, int n, int nL) {
+  double num = 0.0;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) {
+    if (c < C) {
+      const double dd = __int2double_rn(n * L[c] - N[c] * nL);
+      num = __dadd_rn(num, __dmul_rn(dd, dd));
+    }
+  }
+  const double g = __ddiv_rn(num, __dmul_rn(__int2double_rn(nL), __int2double_rn(n - nL)));
+  return __ddiv_rn(g, __dmul_rn(__int2double_rn(n), __int2double_rn(n)));
+}
+__device__ __forceinline__ float key32s(const Crit& cr, const int* L, const int* N, int C, int n, int nL) {
+  return cr.ent ? ent_key32_small(L, N, C, n, nL) : gain32_small(L, N, C, n, nL);
+}
+__device__ __forceinline__ double gain64s(const Crit& cr, const int* L, const int* N, int C, int n, int nL) {
+  return cr.ent ? ent_gain64_small(L, N, C, n, nL, cr.tab) : gain64_small(L, N, C, n, nL);
 }
 __device__ __forceinline__ double gain64c(const Crit& cr, const int* L, const int* N, int C, int64_t n,
                                           int64_t nL) {

@@ -180,7 +180,7 @@ __device__ __forceinline__ void scan_candidates(const unsigned long long (&k)[EP
         int L[kMaxClasses];
 #pragma unroll
         for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
-        visit(e, run, key32(cr, L, nc.N, C, nc.nv, e + 1), a, b);
+        visit(e, run, key32s(cr, L, nc.N, C, nc.nv, e + 1), a, b);
       }
     }
   }
@@ -245,7 +245,7 @@ __device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, c
         int L[kMaxClasses];
 #pragma unroll
         for (int cc = 0; cc < kMaxClasses; ++cc) L[cc] = pc_get(run, cc);
-        const Cand c{gain64c(cr, L, nc.N, C, nc.nv, e + 1), 0, e};
+        const Cand c{gain64s(cr, L, nc.N, C, nc.nv, e + 1), 0, e};
         if (better(c, lb.c)) {
           lb.c = c;
           lb.ka = a;
@@ -404,7 +404,7 @@ __device__ __forceinline__ void sc_walk(const unsigned long long* keys, const So
       int L[kMaxClasses];
 #pragma unroll
       for (int c = 0; c < kMaxClasses; ++c) L[c] = pc_get(run, c);
-      visit(i, run, key32(cr, L, nc.N, C, nc.nv, i + 1), a, b);
+      visit(i, run, key32s(cr, L, nc.N, C, nc.nv, i + 1), a, b);
     }
   }
 }
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const
           int L[kMaxClasses];
 #pragma unroll
           for (int cc = 0; cc < kMaxClasses; ++cc) L[cc] = pc_get(r, cc);
-          const Cand c{gain64c(cr, L, nc.N, ds.C, nc.nv, i + 1), 0, i};
+          const Cand c{gain64s(cr, L, nc.N, ds.C, nc.nv, i + 1), 0, i};
           if (better(c, lb.c)) {
             lb.c = c;
             lb.ka = a;
