@@ -141,6 +141,8 @@ struct SearchScratch {
   int32_t* err = nullptr;       // [m+1] per-node bad-input flags
   void* sort_res = nullptr;     // [m*P] per-(exact-path node, projection) results
   int32_t* node_cls = nullptr;  // [m*8] class counts of exact-path nodes
+  int64_t* sort_lists = nullptr;  // [2][m*P] exact-path pairs to re-score in double
+  int32_t* sort_list_n = nullptr; // [2] their counts
   int64_t m_hist_cap = 0;
   StagedScratch staged;
   RwTables rw;                  // random-width rule only
@@ -193,8 +195,8 @@ struct Crit {
 };
 
 cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan_total, const int32_t* tiny,
-                             const int32_t* med,
-                             void* res, int32_t* node_cls, cudaStream_t st);
+                             const int32_t* med, void* res, int32_t* node_cls, int64_t* lists, int32_t* list_n,
+                             cudaStream_t st);
 size_t sort_res_bytes();
 
 // staged-tile histogram path (features up to 65536)

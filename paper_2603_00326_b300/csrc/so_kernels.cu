@@ -553,6 +553,8 @@ void carve_search(Carver& cv, SearchScratch& s, int32_t m, int64_t n_total, int3
   s.err = cv.take<int32_t>((size_t)m + 1);  // per-node bad-row flags
   s.sort_res = cv.take<unsigned char>((size_t)m * P * sort_res_bytes());
   s.node_cls = cv.take<int32_t>((size_t)m * kMaxClasses);
+  s.sort_lists = cv.take<int64_t>(2 * (size_t)m * P + 2);
+  s.sort_list_n = cv.take<int32_t>(2);
   s.mm_keys = cv.take<uint32_t>((size_t)mh * P * 2);
   s.max32 = cv.take<float>((size_t)mh * P);
   s.node_counts = cv.take<int32_t>((size_t)mh * C);
@@ -660,7 +662,8 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
                                              s.mm_keys, rw ? s.rw.t : nullptr, cr, a.out, a.left_counts);
   }
   // exact path
-  e = launch_sort_warp(a, cr, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls, st);
+  e = launch_sort_warp(a, cr, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls,
+                       s.sort_lists, s.sort_list_n, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -6,11 +6,14 @@
 // of up to kSortRegMax samples (bitonic network, lane-major layout
 // e = lane*EPL + r), one CTA in shared memory for larger exact-path nodes --
 // form class prefix counts with a packed scan, evaluate the float key of the
-// criterion at every boundary between distinct values, take the projection's float
-// maximum M_p, re-score in double every candidate within the criterion's
-// window below M_p (Gini: M_p(1-eps); information gain: an absolute bound
-// of the key's error) and store the projection's lexicographic best (double
-// gain, lowest position).
+// criterion at every boundary between distinct values and keep the
+// projection's float maximum M_p.  k_sort_node_thr then sets each node's
+// window below M = max_p M_p, and a second pass redoes only the projections
+// with M_p inside it (the only ones the selection reads; the double re-score
+// is the costly part on this GPU), re-scoring in double every candidate
+// within the window below its own M_p (Gini: M_p(1-eps); information gain:
+// an absolute bound of the key's error) and storing the projection's
+// lexicographic best (double gain, lowest position).
 // Pass 2 (k_sortw_select): one warp per node takes M = max_p M_p and the
 // lexicographic best (gain, projection, position) over the projections whose
 // M_p lies in the same window below M.  The double winner of the node is
@@ -187,6 +190,13 @@ __device__ __forceinline__ void scan_candidates(const unsigned long long (&k)[EP
 }
 
 // Node context from its offsets and the class counts computed once per node.
+__device__ __forceinline__ void node_ctx_j(const int64_t* off, int j, const int32_t* __restrict__ node_cls,
+                                           SortNodeCtx& nc) {
+  nc.beg = off[j];
+  nc.nv = (int)(off[j + 1] - nc.beg);
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) nc.N[c] = node_cls[(int64_t)j * kMaxClasses + c];
+}
 __device__ __forceinline__ void node_ctx(const int64_t* off, const int32_t* nodes, int64_t s,
                                          const int32_t* __restrict__ node_cls, SortNodeCtx& nc, int& j) {
   j = nodes[s];
@@ -230,7 +240,7 @@ __device__ __forceinline__ void best_reduce(Best& lb) {
 // candidate walker walk(visit); writes the projection's SortRes.
 template <class Walk>
 __device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, const Crit& cr, int lane, Walk walk,
-                                                 SortRes* out) {
+                                                 bool rescore, SortRes* out) {
   float m = key_none(cr);
   walk([&](int, const PackedCnt&, float g, unsigned, unsigned) { m = fmaxf(m, g); });
   m = warp_max(m);
@@ -238,7 +248,7 @@ __device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, c
   lb.c = Cand{-1.0, INT_MAX, INT_MAX};
   lb.ka = lb.kb = 0u;
   lb.L = PackedCnt{0, 0};
-  if (key_any(cr, m)) {
+  if (rescore && key_any(cr, m)) {
     const float thr = key_thr(cr, m, nc.nv, C);
     walk([&](int e, const PackedCnt& run, float g, unsigned a, unsigned b) {
       if (g >= thr) {
@@ -271,11 +281,12 @@ __device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, c
 
 template <int EPL>
 __device__ __forceinline__ void proj_pass1_reg(const DatasetView& ds, const int32_t* idx, const ProjView& pv, int64_t q,
-                                               const SortNodeCtx& nc, int lane, const Crit& cr, SortRes* out) {
+                                               const SortNodeCtx& nc, int lane, const Crit& cr, bool rescore,
+                                               SortRes* out) {
   unsigned long long k[EPL];
   load_sort<EPL>(ds, idx, pv, q, nc, lane, k);
   score_projection(nc, ds.C, cr, lane, [&](auto visit) { scan_candidates<EPL>(k, nc, ds.C, cr, lane, visit); },
-                   out);
+                   rescore, out);
 }
 
 __device__ __forceinline__ int epl_of(int nv) { return nv <= 32 ? 1 : nv <= 64 ? 2 : 4; }
@@ -284,32 +295,45 @@ __device__ __forceinline__ int epl_of(int nv) { return nv <= 32 ? 1 : nv <= 64 ?
 
 // Pass 1, register form: one warp per (node of <= kSortRegMax samples,
 // projection).  ENT fixes the criterion at compile time, so the Gini form
-// carries none of the information gain's code.
+// carries none of the information gain's code.  With node_thr null the pass
+// keeps only each projection's float maximum; with node_thr it redoes, with
+// the double re-score, only the projections whose maximum reaches their
+// node's window (listed by k_sort_node_thr) -- the only ones the selection
+// reads.
 template <int ENT>
 __global__ void __launch_bounds__(256, 4) k_sortw_scan(DatasetView ds, const int32_t* __restrict__ idx,
                                                        const int64_t* __restrict__ off, ProjView pv,
                                                        const V4* plan_total, const int32_t* nodes,
                                                        const int32_t* __restrict__ node_cls, Crit cr_in,
-                                                       SortRes* res) {
+                                                       SortRes* res, const int64_t* __restrict__ list,
+                                                       const int32_t* __restrict__ list_n) {
   Crit cr = cr_in;
   cr.ent = ENT;
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int P = pv.P;
-  const int64_t total = plan_total->y * P;
+  const bool rescore = list != nullptr;
+  const int64_t total = rescore ? (int64_t)*list_n : plan_total->y * P;
   for (int64_t t = gw; t < total; t += nw) {
-    const int64_t s = t / P;
-    const int p = (int)(t - s * P);
     SortNodeCtx nc;
-    int j;
-    node_ctx(off, nodes, s, node_cls, nc, j);
+    int j, p;
+    if (rescore) {
+      const int64_t q = list[t];
+      j = (int)(q / P);
+      p = (int)(q - (int64_t)j * P);
+      node_ctx_j(off, j, node_cls, nc);
+    } else {
+      const int64_t s = t / P;
+      p = (int)(t - s * P);
+      node_ctx(off, nodes, s, node_cls, nc, j);
+    }
     const int64_t q = (int64_t)j * P + p;
     SortRes* out = res + q;
     switch (epl_of(nc.nv)) {
-      case 1: proj_pass1_reg<1>(ds, idx, pv, q, nc, lane, cr, out); break;
-      case 2: proj_pass1_reg<2>(ds, idx, pv, q, nc, lane, cr, out); break;
-      default: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, cr, out); break;
+      case 1: proj_pass1_reg<1>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
+      case 2: proj_pass1_reg<2>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
+      default: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
     }
   }
 }
@@ -414,20 +438,31 @@ __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const
                                                           const int64_t* __restrict__ off, ProjView pv,
                                                           const V4* plan_total, const int32_t* nodes,
                                                           const int32_t* __restrict__ node_cls, Crit cr_in,
-                                                          SortRes* res) {
+                                                          SortRes* res, const int64_t* __restrict__ list,
+                                                          const int32_t* __restrict__ list_n, int inline_rescore) {
   Crit cr = cr_in;
   cr.ent = ENT;
+  // as k_sortw_scan, or in one pass with the re-score inline (the sort, not
+  // the double re-score, dominates a CTA-sorted node)
+  const bool rescore = list != nullptr || inline_rescore;
   extern __shared__ unsigned long long s_keys[];  // [NP <= kMaxSortBelow]
   __shared__ ScShared sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = pv.P;
-  const int64_t total = plan_total->w * P;
+  const int64_t total = list ? (int64_t)*list_n : plan_total->w * P;
   for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-    const int64_t s = t / P;
-    const int p = (int)(t - s * P);
     SortNodeCtx nc;
-    int j;
-    node_ctx(off, nodes, s, node_cls, nc, j);
+    int j, p;
+    if (list) {
+      const int64_t q = list[t];
+      j = (int)(q / P);
+      p = (int)(q - (int64_t)j * P);
+      node_ctx_j(off, j, node_cls, nc);
+    } else {
+      const int64_t s = t / P;
+      p = (int)(t - s * P);
+      node_ctx(off, nodes, s, node_cls, nc, j);
+    }
     const int64_t q = (int64_t)j * P + p;
     int NP = 2 * kScThreads;
     while (NP < nc.nv) NP <<= 1;
@@ -484,7 +519,7 @@ __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const
     lb.c = Cand{-1.0, INT_MAX, INT_MAX};
     lb.ka = lb.kb = 0u;
     lb.L = PackedCnt{0, 0};
-    if (key_any(cr, m)) {
+    if (rescore && key_any(cr, m)) {
       const float thr = key_thr(cr, m, nc.nv, ds.C);
       sc_walk(s_keys, nc, ds.C, cr, i0, E, run, [&](int i, const PackedCnt& r, float g, unsigned a, unsigned b) {
         if (g >= thr) {
@@ -605,27 +640,82 @@ __global__ void __launch_bounds__(256) k_sortw_select(const int64_t* __restrict_
   }
 }
 
+// Between the two passes: each exact-path node's re-score window from its
+// projections' float maxima (+inf when no candidate can win).
+// Lists the (node, projection) pairs whose float maximum reaches the node's
+// window (list 0: register-sorted nodes, list 1: CTA-sorted nodes); the order
+// of a list does not matter, each entry writes its own result.
+__global__ void __launch_bounds__(256) k_sort_node_thr(const int64_t* __restrict__ off, int32_t P, int32_t C,
+                                                       const V4* plan_total, const int32_t* tiny, const int32_t* med,
+                                                       const SortRes* __restrict__ res, Crit cr, int64_t* lists,
+                                                       int64_t list_cap, int32_t* list_n, int list_med) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t m_tiny = plan_total->y, m_all = plan_total->y + plan_total->w;
+  for (int64_t s = gw; s < m_all; s += nw) {
+    const int j = s < m_tiny ? tiny[s] : med[s - m_tiny];
+    const int which = s < m_tiny ? 0 : 1;
+    if (which == 1 && !list_med) continue;
+    const int nv = (int)(off[j + 1] - off[j]);
+    const SortRes* rj = res + (int64_t)j * P;
+    float M = key_none(cr);
+    for (int p = lane; p < P; p += 32) M = fmaxf(M, rj[p].m32);
+    M = warp_max(M);
+    if (!key_any(cr, M)) continue;
+    const float thr = key_thr(cr, M, nv, C);
+    for (int p0 = 0; p0 < P; p0 += 32) {
+      const int p = p0 + lane;
+      const bool in = p < P && rj[p].m32 >= thr;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&list_n[which], __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (in) {
+        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+        if (pos < list_cap) lists[which * list_cap + pos] = (int64_t)j * P + p;
+      }
+    }
+  }
+}
+
 cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan_total, const int32_t* tiny,
-                             const int32_t* med, void* res_raw, int32_t* node_cls, cudaStream_t st) {
+                             const int32_t* med, void* res_raw, int32_t* node_cls, int64_t* lists,
+                             int32_t* list_n, cudaStream_t st) {
   const DeviceInfo& di = device_info();
   SortRes* res = static_cast<SortRes*>(res_raw);
+  const int64_t list_cap = (int64_t)a.m * a.pv.P;
+  cudaError_t e = cudaMemsetAsync(list_n, 0, 2 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
   {
     ProfScope ps_("k_sortw_counts", st);
     k_sortw_counts<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, plan_total, tiny, med, node_cls);
   }
-  {
-    ProfScope ps_("k_sortw_scan", st);
-    auto kern = cr.ent ? k_sortw_scan<1> : k_sortw_scan<0>;
-    kern<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, tiny, node_cls, cr, res);
-  }
-  if (!a.hist_only && a.T > kSortRegMax + 1) {
-    int NPmax = 2 * kScThreads;
-    while (NPmax < a.T - 1) NPmax <<= 1;
-    const size_t smem = (size_t)NPmax * 8;
-    ProfScope ps_("k_sortc_scan", st);
-    auto kern = cr.ent ? k_sortc_scan<1> : k_sortc_scan<0>;
-    kern<<<di.num_sms * 16, kScThreads, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, med, node_cls, cr,
-                                                    res);
+  const bool cta = !a.hist_only && a.T > kSortRegMax + 1;
+  int NPmax = 2 * kScThreads;
+  while (NPmax < a.T - 1) NPmax <<= 1;
+  const size_t smem = (size_t)NPmax * 8;
+  auto kw = cr.ent ? k_sortw_scan<1> : k_sortw_scan<0>;
+  auto kc = cr.ent ? k_sortc_scan<1> : k_sortc_scan<0>;
+  // every projection's float maximum; then each node's window; then the
+  // double re-score of the projections inside their node's window only
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t* lw = pass == 0 ? nullptr : lists;
+    {
+      ProfScope ps_("k_sortw_scan", st);
+      kw<<<di.num_sms * 8, 256, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, tiny, node_cls, cr, res, lw,
+                                         list_n);
+    }
+    if (cta && pass == 0) {  // CTA-sorted nodes: one pass, re-score inline
+      ProfScope ps_("k_sortc_scan", st);
+      kc<<<di.num_sms * 16, kScThreads, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, med, node_cls, cr,
+                                                    res, nullptr, list_n + 1, 1);
+    }
+    if (pass == 0) {
+      ProfScope ps_("k_sort_node_thr", st);
+      k_sort_node_thr<<<di.num_sms * 4, 256, 0, st>>>(a.node_off, a.pv.P, a.ds.C, plan_total, tiny, med, res, cr,
+                                                      lists, list_cap, list_n, 0);
+    }
   }
   {
     ProfScope ps_("k_sortw_select", st);
