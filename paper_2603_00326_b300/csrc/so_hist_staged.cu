@@ -152,7 +152,20 @@ struct StagedPlan {
   const V4* item_total;     // lane: items of this kernel
   int lane;                 // 0: min/max items (x), 1: histogram items (y)
   int64_t S;                // samples per chunk
+  unsigned long long* ctr;  // next item to take (zeroed before the launch)
 };
+
+// Items are taken from a counter, so a CTA that drew short items takes more
+// (items differ a lot in size: chunks of large nodes and whole small ones).
+// Every item's output is order-independent (atomic min / max and histogram
+// flushes, projected values at fixed positions).  The caller's barrier
+// comes first: every thread has read the previous item number.
+__device__ __forceinline__ int64_t next_item(const StagedPlan& sp, int64_t* s_item) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_item = (int64_t)atomicAdd(sp.ctr, 1ull);
+  __syncthreads();
+  return *s_item;
+}
 
 __device__ __forceinline__ int64_t items_total(const StagedPlan& sp) {
   const V4 t = *sp.item_total;
@@ -754,7 +767,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = pv.P;
   const int64_t n_items = items_total(sp);
-  for (int64_t t = blockIdx.x; t < n_items; t += gridDim.x) {
+  __shared__ int64_t s_item;
+  for (int64_t t = next_item(sp, &s_item); t < n_items; t = next_item(sp, &s_item)) {
     const ItemPos it = decode_item(sp, t, P);
     const int64_t qbase = (int64_t)it.j * P + it.p0;
     __syncthreads();  // previous item done with shared memory
@@ -1134,7 +1148,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   const unsigned limit = (unsigned)(npair * HS) * 4u;  // byte offset of the trash word
   const unsigned magic_bits = __float_as_uint(kMagic);
   const int64_t n_items = items_total(sp);
-  for (int64_t t = blockIdx.x; t < n_items; t += gridDim.x) {
+  __shared__ int64_t s_item;
+  for (int64_t t = next_item(sp, &s_item); t < n_items; t = next_item(sp, &s_item)) {
     const ItemPos it = decode_item(sp, t, P);
     const int64_t qbase = (int64_t)it.j * P + it.p0;
     __syncthreads();  // previous item's flush finished
@@ -1294,6 +1309,7 @@ void carve_staged(Carver& cv, StagedScratch& s, int64_t m_hist_cap, int P) {
   s.item_off2 = cv.take<int64_t>(m_hist_cap + 1);
   s.item_total = cv.take<V4>(1);
   s.tiles = cv.take<V4>(scan_tiles_for(m_hist_cap) + 1);
+  s.item_ctr = cv.take<unsigned long long>(2);
 }
 
 template <int KMAX>
@@ -1340,8 +1356,12 @@ cudaError_t launch_staged_k(const SearchArgs& a, const V4* plan_total, const int
   ItemScanF isf{plan_total, hist_nodes, a.node_off, ss.ng1, ss.ng2, S1, S2, ss.item_off1, ss.item_off2};
   e = run_scan(isf, m_hist_cap, ss.tiles, ss.item_total, st, "item_scan");
   if (e != cudaSuccess) return e;
-  StagedPlan sp1{plan_total, hist_nodes, a.node_off, ss.ng1, ss.gs1, ss.item_off1, ss.item_total, 0, S1};
-  StagedPlan sp2{plan_total, hist_nodes, a.node_off, ss.ng2, ss.gs2, ss.item_off2, ss.item_total, 1, S2};
+  e = cudaMemsetAsync(ss.item_ctr, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  StagedPlan sp1{plan_total, hist_nodes, a.node_off, ss.ng1, ss.gs1, ss.item_off1, ss.item_total, 0, S1,
+                 ss.item_ctr};
+  StagedPlan sp2{plan_total, hist_nodes, a.node_off, ss.ng2, ss.gs2, ss.item_off2, ss.item_total, 1, S2,
+                 ss.item_ctr + 1};
   {
     const size_t smem = mm_smem_bytes(d, KMAX);
     e = cudaFuncSetAttribute(k_mm_staged<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -125,6 +125,7 @@ struct StagedScratch {
   int64_t* item_off2 = nullptr;
   V4* item_total = nullptr;
   V4* tiles = nullptr;
+  unsigned long long* item_ctr = nullptr;  // [2] dynamic item counters of the two kernels
 };
 
 // Device scratch of one search (carved from a workspace).
