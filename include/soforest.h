@@ -277,8 +277,10 @@ so_status so_histograms(const so_dataset *ds, const int32_t *idx, int64_t n_tota
 
 /* Tree growth parameters.
  *  n_bins, sort_below, hist_only, rescore_rel_eps, bin_rule, criterion,
- *             proj_per_cta, chunk  as in so_split_params; random-width
- *             boundaries use the tree's node keys.
+ *             proj_per_cta, chunk  as in so_split_params, except that chunk 0
+ *             means 4096 here (a tree's histogram nodes are mostly gathered
+ *             nodes of a few thousand samples); random-width boundaries use the
+ *             tree's node keys.
  *  n_proj     projections sampled per node, 1..1024.
  *  lambda, nnz_cap  nnz law of a projection: min(nnz_cap, d, 1+Poisson(lambda)).
  *  seed, tree_id    root key = splitmix64(seed ^ tree_id*0x9E3779B97F4A7C15);

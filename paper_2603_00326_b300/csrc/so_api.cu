@@ -749,7 +749,9 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
           a.bin_rule = tp->bin_rule;
           a.bin_keys = cur.key + j0;  // random-width boundaries from the node keys
           a.criterion = tp->criterion;
-          apply_tuning(a, tp->proj_per_cta, tp->chunk);
+          // most histogram-path nodes of a tree are gathered nodes of a few
+          // thousand samples: smaller items balance the SMs better
+          apply_tuning(a, tp->proj_per_cta, tp->chunk > 0 ? tp->chunk : 4096);
           e = launch_search(a, ss, ls);
           if (e == cudaSuccess)
             e = launch_tree_record_splits((int32_t)j0, mb, cur, spl, snnz, sfeat, ssign, P, cap, td, ls);
