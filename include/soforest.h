@@ -265,8 +265,10 @@ so_status so_sample_projections(int32_t m, const uint64_t *keys, int32_t n_proj,
  *  params      n_bins, bin_rule and bin_keys are used; the rest is ignored.
  *  minmax_dev  device float [m*n_proj*2]: (min, max) of each projection.
  *  hist_dev    device int32 [m*n_proj*n_bins*n_classes] class counts per bin.
- *  gain32_dev  device float [m*n_proj*(n_bins-1)] float gain of every
- *              candidate (-1 where a side is empty), or NULL.
+ *  gain32_dev  device float [m*n_proj*(n_bins-1)] float Gini gain of every
+ *              candidate without the 1/n^2 factor, sum_c D_c^2 / (nL nR)
+ *              (-1 where a side is empty), or NULL; Gini whatever
+ *              params->criterion says.
  *  bounds_dev  device float [m*n_proj*(n_bins-1)] boundaries t_1..t_{B-1}
  *              of every projection, or NULL.
  * Asynchronous; uses the internal arena. */

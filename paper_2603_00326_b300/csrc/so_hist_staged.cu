@@ -1273,7 +1273,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
 // ---- host side ----------------------------------------------------------------
 int hist_group_size(int B, int C, bool rw) {
   // 16-bit counters, two projections per word, plus the random-width tables
-  // (boundaries and guide of each projection), in <= 100 KB of shared memory.
+  // (boundaries and guide of each projection), in about 100 KB of shared
+  // memory (a first estimate: the launch shrinks the group until the CTA's
+  // whole shared memory fits the device limit).
   // Rounded down to a multiple of the 32 warps when at least 32: a group of,
   // say, 36 gives 4 warps two projections while 28 wait at every barrier.
   const int pair_bytes = (B + 1) * C * 4 + (rw ? 2 * kRwRow * 6 : 0);
