@@ -355,10 +355,19 @@ struct ScShared {
   Best wbest[kScWarps];
 };
 
+// Shared-memory slot of sorted position p: bits 0-3 are XORed with bits 4-7,
+// so that a warp reading each thread's run of E = 2..16 consecutive positions
+// touches 16 distinct 8-byte bank pairs per half-warp, while every aligned run
+// of 16 positions stays a permutation of its own 16 slots (the sort's access
+// pattern keeps its bank spread).
+__device__ __forceinline__ int sc_slot(int p) { return p ^ ((p >> 4) & 15); }
+
+// Writes the node's nv (key, label) pairs to positions 0..nv-1 (the sort
+// never reads positions >= nv; see sc_bitonic).
 __device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* __restrict__ idx, const SortNodeCtx& nc,
-                                          int NP, int kk, const ScShared& sh, unsigned long long* keys) {
+                                          int kk, const ScShared& sh, unsigned long long* keys) {
   constexpr int kPer = 4;  // samples per thread per round, loads of 4 terms in flight per sample
-  for (int e0 = threadIdx.x; e0 < NP; e0 += kScThreads * kPer) {
+  for (int e0 = threadIdx.x; e0 < nc.nv; e0 += kScThreads * kPer) {
     int64_t sid[kPer];
     float v[kPer];
 #pragma unroll
@@ -387,24 +396,33 @@ __device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* 
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = e0 + u * kScThreads;
-      if (e < NP)
-        keys[e] = sid[u] >= 0 ? (((unsigned long long)f2key(v[u]) << 32) | (unsigned long long)(unsigned)ds.y[sid[u]])
-                              : ~0ull;
+      if (sid[u] >= 0) keys[sc_slot(e)] = ((unsigned long long)f2key(v[u]) << 32) | (unsigned long long)(unsigned)ds.y[sid[u]];
     }
   }
 }
 
-__device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP) {
+// Ascending bitonic network over NP = 2^k positions of which the first nv
+// hold keys: each merge of blocks of `size` first compares offset o of a
+// block with its mirror size-1-o, then half-cleans with strides size/4 .. 1,
+// every comparator putting the smaller key at the lower position.  Positions
+// >= nv act as keys above every real key (a real key's label byte keeps it
+// below all-ones), so no comparator ever moves a real key there: a
+// comparator whose upper position is >= nv is a no-op and is skipped, and
+// those positions are never read or written.
+__device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP, int nv) {
   for (int size = 2; size <= NP; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+    const int half = size >> 1;
+    for (int stride = half; stride > 0; stride >>= 1) {
       for (int i = threadIdx.x; i < NP / 2; i += kScThreads) {
-        const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool up = (lo & size) == 0;
-        const unsigned long long a = keys[lo], b = keys[hi];
-        if ((a > b) == up) {
-          keys[lo] = b;
-          keys[hi] = a;
+        const int o = i & (stride - 1);
+        const int lo = ((i & ~(stride - 1)) << 1) | o;
+        const int hi = stride == half ? lo + size - 1 - 2 * o : lo + stride;
+        if (hi >= nv) continue;
+        const int sl = sc_slot(lo), sh = sc_slot(hi);
+        const unsigned long long a = keys[sl], b = keys[sh];
+        if (a > b) {
+          keys[sl] = b;
+          keys[sh] = a;
         }
       }
       __syncthreads();
@@ -418,12 +436,14 @@ __device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP) {
 template <class Visit>
 __device__ __forceinline__ void sc_walk(const unsigned long long* keys, const SortNodeCtx& nc, int C, const Crit& cr,
                                         int i0, int E, PackedCnt run, Visit visit) {
+  unsigned long long x = i0 < nc.nv - 1 ? keys[sc_slot(i0)] : 0ull;
   for (int e = 0; e < E; ++e) {
     const int i = i0 + e;
     if (i >= nc.nv - 1) break;
-    const unsigned long long x = keys[i];
+    const unsigned long long nx = keys[sc_slot(i + 1)];
     pc_add(run, (int)(x & 0xFFull));
-    const unsigned a = (unsigned)(x >> 32), b = (unsigned)(keys[i + 1] >> 32);
+    const unsigned a = (unsigned)(x >> 32), b = (unsigned)(nx >> 32);
+    x = nx;
     if (a != b) {
       int L[kMaxClasses];
 #pragma unroll
@@ -476,15 +496,15 @@ __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const
       sh.sign[threadIdx.x] = pv.sign[rb + threadIdx.x];
     }
     __syncthreads();
-    sc_gather(ds, idx, nc, NP, kk, sh, s_keys);
+    sc_gather(ds, idx, nc, kk, sh, s_keys);
     __syncthreads();
-    sc_bitonic(s_keys, NP);
+    sc_bitonic(s_keys, NP, nc.nv);
     // this thread's chunk of consecutive sorted positions and its left counts
     const int E = NP / kScThreads;
     const int i0 = threadIdx.x * E;
     PackedCnt own{0, 0};
     for (int e = 0; e < E; ++e)
-      if (i0 + e < nc.nv) pc_add(own, (int)(s_keys[i0 + e] & 0xFFull));
+      if (i0 + e < nc.nv) pc_add(own, (int)(s_keys[sc_slot(i0 + e)] & 0xFFull));
     unsigned long long ilo = own.lo, ihi = own.hi;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
