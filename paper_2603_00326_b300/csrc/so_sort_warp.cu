@@ -408,11 +408,51 @@ __device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* 
 // >= nv act as keys above every real key (a real key's label byte keeps it
 // below all-ones), so no comparator ever moves a real key there: a
 // comparator whose upper position is >= nv is a no-op and is skipped, and
-// those positions are never read or written.
+// those positions are never written (nor read: registers stand in all-ones).
+// Comparators within an aligned run of kScRun positions run in registers, one
+// thread per run (the whole network for sizes up to kScRun, then strides
+// kScRun/2 .. 1 of every larger merge); the other strides are shared-memory
+// stages with a barrier each.
+constexpr int kScRun = 8;
+
+template <bool kWhole>
+__device__ __forceinline__ void sc_runs(unsigned long long* keys, int NP, int nv) {
+  for (int b = threadIdx.x; b < NP / kScRun; b += kScThreads) {
+    const int base = b * kScRun;
+    if (base >= nv) break;
+    unsigned long long r[kScRun];
+#pragma unroll
+    for (int u = 0; u < kScRun; ++u) r[u] = base + u < nv ? keys[sc_slot(base + u)] : ~0ull;
+#pragma unroll
+    for (int size = kWhole ? 2 : 2 * kScRun; size <= (kWhole ? kScRun : 2 * kScRun); size <<= 1) {
+      const int half = size >> 1;
+#pragma unroll
+      for (int stride = half < kScRun ? half : kScRun / 2; stride > 0; stride >>= 1) {
+#pragma unroll
+        for (int u = 0; u < kScRun; ++u) {
+          const int o = u & (stride - 1);
+          if ((u & stride) == 0) {
+            // mirror comparator (first stage of a merge that fits the run) or half-cleaner
+            const int w = (kWhole && stride == half) ? (u | (size - 1)) - o : u + stride;
+            const unsigned long long a = r[u], c = r[w];
+            r[u] = a < c ? a : c;
+            r[w] = a < c ? c : a;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kScRun; ++u)
+      if (base + u < nv) keys[sc_slot(base + u)] = r[u];
+  }
+}
+
 __device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP, int nv) {
-  for (int size = 2; size <= NP; size <<= 1) {
+  sc_runs<true>(keys, NP, nv);
+  __syncthreads();
+  for (int size = 2 * kScRun; size <= NP; size <<= 1) {
     const int half = size >> 1;
-    for (int stride = half; stride > 0; stride >>= 1) {
+    for (int stride = half; stride >= kScRun; stride >>= 1) {
       for (int i = threadIdx.x; i < NP / 2; i += kScThreads) {
         const int o = i & (stride - 1);
         const int lo = ((i & ~(stride - 1)) << 1) | o;
@@ -427,6 +467,8 @@ __device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP, int
       }
       __syncthreads();
     }
+    sc_runs<false>(keys, NP, nv);
+    __syncthreads();
   }
 }
 
