@@ -364,6 +364,10 @@ __device__ __forceinline__ int sc_slot(int p) { return p ^ ((p >> 4) & 15); }
 
 // Writes the node's nv (key, label) pairs to positions 0..nv-1 (the sort
 // never reads positions >= nv; see sc_bitonic).
+// RM: read the row-major copy ds.Xr (the node's projections then share its
+// samples' rows through L2) instead of one sector per (sample, feature) of
+// the columns.
+template <int RM>
 __device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* __restrict__ idx, const SortNodeCtx& nc,
                                           int kk, const ScShared& sh, unsigned long long* keys) {
   constexpr int kPer = 4;  // samples per thread per round, loads of 4 terms in flight per sample
@@ -380,9 +384,11 @@ __device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* 
       float x[4][kPer];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
-        const float* col = ds.X + (int64_t)sh.feat[j0 + jj < kk ? j0 + jj : j0] * ds.ld;
+        const int64_t f = sh.feat[j0 + jj < kk ? j0 + jj : j0];
+        const float* col = RM ? ds.Xr + f : ds.X + f * ds.ld;
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) x[jj][u] = (j0 + jj < kk && sid[u] >= 0) ? __ldg(col + sid[u]) : 0.0f;
+        for (int u = 0; u < kPer; ++u)
+          x[jj][u] = (j0 + jj < kk && sid[u] >= 0) ? __ldg(col + (RM ? sid[u] * ds.d : sid[u])) : 0.0f;
       }
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
@@ -495,8 +501,9 @@ __device__ __forceinline__ void sc_walk(const unsigned long long* keys, const So
   }
 }
 
-template <int ENT>
-__global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const int32_t* __restrict__ idx,
+// Eight CTAs per SM (64 registers a thread): the gathers are latency-bound.
+template <int ENT, int RM>
+__global__ void __launch_bounds__(kScThreads, 8) k_sortc_scan(DatasetView ds, const int32_t* __restrict__ idx,
                                                           const int64_t* __restrict__ off, ProjView pv,
                                                           const V4* plan_total, const int32_t* nodes,
                                                           const int32_t* __restrict__ node_cls, Crit cr_in,
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(kScThreads) k_sortc_scan(DatasetView ds, const
       sh.sign[threadIdx.x] = pv.sign[rb + threadIdx.x];
     }
     __syncthreads();
-    sc_gather(ds, idx, nc, kk, sh, s_keys);
+    sc_gather<RM>(ds, idx, nc, kk, sh, s_keys);
     __syncthreads();
     sc_bitonic(s_keys, NP, nc.nv);
     // this thread's chunk of consecutive sorted positions and its left counts
@@ -758,7 +765,8 @@ cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan
   while (NPmax < a.T - 1) NPmax <<= 1;
   const size_t smem = (size_t)NPmax * 8;
   auto kw = cr.ent ? k_sortw_scan<1> : k_sortw_scan<0>;
-  auto kc = cr.ent ? k_sortc_scan<1> : k_sortc_scan<0>;
+  auto kc = cr.ent ? (a.ds.Xr ? k_sortc_scan<1, 1> : k_sortc_scan<1, 0>)
+                   : (a.ds.Xr ? k_sortc_scan<0, 1> : k_sortc_scan<0, 0>);
   // every projection's float maximum; then each node's window; then the
   // double re-score of the projections inside their node's window only
   for (int pass = 0; pass < 2; ++pass) {
