@@ -658,6 +658,41 @@ __device__ __forceinline__ void project_tile(unsigned tile, unsigned dpk, int k,
   }
 }
 
+// Packed form of project_tile: sample pairs in FP32x2 registers (fma(+-1, x,
+// acc) per lane of the pair, the same single rounding).
+template <int V, int NQ>
+__device__ __forceinline__ void project_tile2(unsigned tile, unsigned dpk, int k, int lane,
+                                              float2 (&acc)[V * NQ / 2]) {
+  const unsigned base = tile + 4u * V * lane;
+#pragma unroll
+  for (int i = 0; i < V * NQ / 2; ++i) acc[i] = make_float2(0.0f, 0.0f);
+  auto term = [&](uint32_t w) {
+    const float s = desc_sign(w);
+    const float2 s2 = make_float2(s, s);
+    const unsigned row = base + (w & 0xffffu);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (V == 4) {
+        const float4 x = lds_f4(row + 512 * q);
+        acc[2 * q] = ffma2(s2, make_float2(x.x, x.y), acc[2 * q]);
+        acc[2 * q + 1] = ffma2(s2, make_float2(x.z, x.w), acc[2 * q + 1]);
+      } else {
+        acc[q] = ffma2(s2, lds_f2(row + 256 * q), acc[q]);
+      }
+    }
+  };
+  for (int j0 = 0; j0 < k; j0 += 4) {
+    const uint4 w = lds_u4(dpk + 4u * j0);
+    term(w.x);
+    if (j0 + 1 >= k) break;
+    term(w.y);
+    if (j0 + 2 >= k) break;
+    term(w.z);
+    if (j0 + 3 >= k) break;
+    term(w.w);
+  }
+}
+
 // Label byte offsets (class * 4) of the lane's samples, in project_tile's
 // order, from the item's label bytes (0xFF marks padding and labels outside
 // [0, C); those get a very negative offset that the address clamp sends to
@@ -694,11 +729,13 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
   constexpr int St = 32 * V * NQ;
   const int ntile = (int)((it.end - it.beg + St - 1) / St);
   const int* my = s_assign + warp * nslot;
-  for (int sl = 0; sl < nslot; ++sl) {
-    const int pl = my[sl];
-    if (pl < 0) break;
-    s_pmin[pl * 32 + lane] = INFINITY;
-    s_pmax[pl * 32 + lane] = -INFINITY;
+  // the lane's running minima and maxima of the warp's projections (at most
+  // kMmPPW) stay in registers over the item's tiles
+  float mns[kMmPPW], mxs[kMmPPW];
+#pragma unroll
+  for (int sl = 0; sl < kMmPPW; ++sl) {
+    mns[sl] = INFINITY;
+    mxs[sl] = -INFINITY;
   }
   const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig, rowmaj, Sp);
   if (ntile > 0) stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
@@ -714,16 +751,16 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
     const unsigned tile = su32(s_tile) + 4u * kTileF * bc;
     bc = bc == 2 ? 0 : bc + 1;
     bi = bi == 2 ? 0 : bi + 1;
-    for (int sl = 0; sl < nslot; ++sl) {
-      const int pl = my[sl];
-      if (pl < 0) break;
-      float acc[V * NQ];
-      project_tile<V, NQ>(tile, su32(s_dpk) + 4u * pl * kmax, s_dk[pl], lane, acc);
-      float mn = s_pmin[pl * 32 + lane], mx = s_pmax[pl * 32 + lane];
 #pragma unroll
-      for (int i = 0; i < V * NQ; ++i) {
-        mn = fminf(mn, acc[i]);
-        mx = fmaxf(mx, acc[i]);
+    for (int sl = 0; sl < kMmPPW; ++sl) {
+      const int pl = sl < nslot ? my[sl] : -1;
+      if (pl < 0) break;
+      float2 acc[V * NQ / 2];
+      project_tile2<V, NQ>(tile, su32(s_dpk) + 4u * pl * kmax, s_dk[pl], lane, acc);
+#pragma unroll
+      for (int i = 0; i < V * NQ / 2; ++i) {
+        mns[sl] = fminf(fminf(mns[sl], acc[i].x), acc[i].y);
+        mxs[sl] = fmaxf(fmaxf(mxs[sl], acc[i].x), acc[i].y);
       }
       if (vbuf) {
         // keep the values for the histogram pass (positions of this node only)
@@ -735,12 +772,18 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
 #pragma unroll
           for (int u = 0; u < V; ++u) {
             const int e = 32 * V * q + V * lane + u;
-            if (e < rem) vp[e] = acc[V * q + u];
+            const float2 a2 = acc[(V * q + u) >> 1];
+            if (e < rem) vp[e] = (u & 1) ? a2.y : a2.x;
           }
       }
-      s_pmin[pl * 32 + lane] = mn;
-      s_pmax[pl * 32 + lane] = mx;
     }
+  }
+#pragma unroll
+  for (int sl = 0; sl < kMmPPW; ++sl) {
+    const int pl = sl < nslot ? my[sl] : -1;
+    if (pl < 0) break;
+    s_pmin[pl * 32 + lane] = mns[sl];
+    s_pmax[pl * 32 + lane] = mxs[sl];
   }
 }
 
@@ -851,40 +894,6 @@ struct BinParams {
   int fast;
 };
 
-// Packed form of project_tile: sample pairs in FP32x2 registers (fma(+-1, x,
-// acc) per lane of the pair, the same single rounding).
-template <int V, int NQ>
-__device__ __forceinline__ void project_tile2(unsigned tile, unsigned dpk, int k, int lane,
-                                              float2 (&acc)[V * NQ / 2]) {
-  const unsigned base = tile + 4u * V * lane;
-#pragma unroll
-  for (int i = 0; i < V * NQ / 2; ++i) acc[i] = make_float2(0.0f, 0.0f);
-  auto term = [&](uint32_t w) {
-    const float s = desc_sign(w);
-    const float2 s2 = make_float2(s, s);
-    const unsigned row = base + (w & 0xffffu);
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      if (V == 4) {
-        const float4 x = lds_f4(row + 512 * q);
-        acc[2 * q] = ffma2(s2, make_float2(x.x, x.y), acc[2 * q]);
-        acc[2 * q + 1] = ffma2(s2, make_float2(x.z, x.w), acc[2 * q + 1]);
-      } else {
-        acc[q] = ffma2(s2, lds_f2(row + 256 * q), acc[q]);
-      }
-    }
-  };
-  for (int j0 = 0; j0 < k; j0 += 4) {
-    const uint4 w = lds_u4(dpk + 4u * j0);
-    term(w.x);
-    if (j0 + 1 >= k) break;
-    term(w.y);
-    if (j0 + 2 >= k) break;
-    term(w.z);
-    if (j0 + 3 >= k) break;
-    term(w.w);
-  }
-}
 
 // Label offsets of the tile (one int per sample, decoded once per tile), in
 // project_tile's order.
