@@ -501,37 +501,28 @@ __device__ __forceinline__ void sc_walk(const unsigned long long* keys, const So
   }
 }
 
-// Eight CTAs per SM (64 registers a thread): the gathers are latency-bound.
+// One pass per (node, projection) with the double re-score inline (the
+// sort, not the re-score, dominates a CTA-sorted node).  Eight CTAs per SM:
+// 64 registers a thread (the row-major form would otherwise take 72).
 template <int ENT, int RM>
 __global__ void __launch_bounds__(kScThreads, 8) k_sortc_scan(DatasetView ds, const int32_t* __restrict__ idx,
-                                                          const int64_t* __restrict__ off, ProjView pv,
-                                                          const V4* plan_total, const int32_t* nodes,
-                                                          const int32_t* __restrict__ node_cls, Crit cr_in,
-                                                          SortRes* res, const int64_t* __restrict__ list,
-                                                          const int32_t* __restrict__ list_n, int inline_rescore) {
+                                                             const int64_t* __restrict__ off, ProjView pv,
+                                                             const V4* plan_total, const int32_t* nodes,
+                                                             const int32_t* __restrict__ node_cls, Crit cr_in,
+                                                             SortRes* res) {
   Crit cr = cr_in;
   cr.ent = ENT;
-  // as k_sortw_scan, or in one pass with the re-score inline (the sort, not
-  // the double re-score, dominates a CTA-sorted node)
-  const bool rescore = list != nullptr || inline_rescore;
   extern __shared__ unsigned long long s_keys[];  // [NP <= kMaxSortBelow]
   __shared__ ScShared sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = pv.P;
-  const int64_t total = list ? (int64_t)*list_n : plan_total->w * P;
+  const int64_t total = plan_total->w * P;
   for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
     SortNodeCtx nc;
-    int j, p;
-    if (list) {
-      const int64_t q = list[t];
-      j = (int)(q / P);
-      p = (int)(q - (int64_t)j * P);
-      node_ctx_j(off, j, node_cls, nc);
-    } else {
-      const int64_t s = t / P;
-      p = (int)(t - s * P);
-      node_ctx(off, nodes, s, node_cls, nc, j);
-    }
+    int j;
+    const int64_t s = t / P;
+    const int p = (int)(t - s * P);
+    node_ctx(off, nodes, s, node_cls, nc, j);
     const int64_t q = (int64_t)j * P + p;
     int NP = 2 * kScThreads;
     while (NP < nc.nv) NP <<= 1;
@@ -588,7 +579,7 @@ __global__ void __launch_bounds__(kScThreads, 8) k_sortc_scan(DatasetView ds, co
     lb.c = Cand{-1.0, INT_MAX, INT_MAX};
     lb.ka = lb.kb = 0u;
     lb.L = PackedCnt{0, 0};
-    if (rescore && key_any(cr, m)) {
+    if (key_any(cr, m)) {
       const float thr = key_thr(cr, m, nc.nv, ds.C);
       sc_walk(s_keys, nc, ds.C, cr, i0, E, run, [&](int i, const PackedCnt& r, float g, unsigned a, unsigned b) {
         if (g >= thr) {
@@ -779,7 +770,7 @@ cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan
     if (cta && pass == 0) {  // CTA-sorted nodes: one pass, re-score inline
       ProfScope ps_("k_sortc_scan", st);
       kc<<<di.num_sms * 16, kScThreads, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, med, node_cls, cr,
-                                                    res, nullptr, list_n + 1, 1);
+                                                    res);
     }
     if (pass == 0) {
       ProfScope ps_("k_sort_node_thr", st);
