@@ -56,8 +56,9 @@ typedef enum {
  * y: device, n labels in [0, n_classes).
  * Xr: optional device row-major copy of the same values, Xr[i*d + f], or
  * NULL.  When given, the min/max pass reads the feature rows of scattered
- * samples from it (one sample's features share DRAM sectors) instead of
- * gathering one sector per (sample, feature) from X; results do not change. */
+ * samples from it, and so does the exact path for nodes of more than 128
+ * samples. One sample's features share DRAM sectors, where X costs one
+ * sector per (sample, feature). Results do not change. */
 typedef struct {
     const float *X;
     int64_t n;          /* samples, 1 .. 2^31-1 */
