@@ -47,7 +47,8 @@ typedef enum {
     SO_EINVAL = 1,     /* bad argument, found on the host before any launch */
     SO_ENOMEM = 2,     /* device or host allocation failed / workspace too small */
     SO_ECUDA = 3,      /* a CUDA runtime call failed */
-    SO_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    SO_ETIMEOUT = 4,   /* reserved for a bounded device-side wait that gives up; no
+                          call returns it: no kernel here waits on another */
     SO_EINTERNAL = 5   /* a device-side consistency check failed */
 } so_status;
 
@@ -215,12 +216,15 @@ so_status so_split_search_batch(const so_dataset *ds, const int32_t *idx, int64_
  * scratch (about n_proj * n_bins * n_classes * 4 bytes of histograms plus a
  * few KiB) exceeds 8 MiB is rejected with SO_EINVAL before any launch.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the array and
- * leaves its contents behind (the kernels initialise what they read); calls
- * that overlap on the GPU, from any stream or thread, race on it.  Keep
- * tracing (so_profile_enable) off: tracing creates CUDA events.  The call
- * synchronises `stream`. */
+ * (cudaGetSymbolAddress) with that device current and caches it until
+ * so_shutdown; after a cudaDeviceReset call so_shutdown before the next call,
+ * so that the address is looked up again.  Every call on a device shares the
+ * array and leaves its contents behind (the kernels initialise what they
+ * read); calls that overlap on the GPU, from any stream or thread, race on
+ * it.  Keep tracing (so_profile_enable) off: tracing creates CUDA events.
+ * The call synchronises `stream` to return the split on the host, so it
+ * cannot be made while `stream` is being captured into a CUDA graph.
+ * Argument errors and CUDA errors are reported as by so_split_search. */
 so_status so_split_search_noalloc(const so_dataset *ds, const int32_t *idx, int64_t n_node,
                                   const so_projs *projs, const so_split_params *params,
                                   so_split *out_host, int64_t *left_counts_host, void *stream);

@@ -804,3 +804,297 @@ int orc_split_search_mt(const float *X, int64_t ld, const uint8_t *y, int C,
     free(jobs); free(th);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Tree to purity with each level's nodes searched on several threads        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The tree of orc_train_tree (R7, Section 2 item 2), grown on n_threads host
+ * threads.  The nodes of one level are independent: a node's split depends
+ * only on its own samples and key.  So each level runs in two phases:
+ *   A. every node is examined, its projections sampled, its split searched
+ *      and its segment stably partitioned in place, in any order on any
+ *      thread; nodes of at least big_node samples one at a time with the
+ *      projections divided over the threads (orc_split_search_mt), the rest
+ *      each on one thread (orc_split_search_rule);
+ *   B. one thread takes the results in breadth-first node order, exactly as
+ *      orc_train_tree does: records, child ids, next-level offsets and the
+ *      copy of each split node's partitioned segment.
+ * The tree is the one orc_train_tree grows, field for field.  Returns 0 or -1.
+ */
+typedef struct {
+    orc_split sp;
+    int64_t N[ORC_MAX_CLASSES];
+    int32_t k, searched, maj;
+    int32_t feat[ORC_MAX_CAP];
+    int8_t sign[ORC_MAX_CAP];
+} orc_node_res;
+
+typedef struct {
+    const float *X; int64_t ld; int32_t d; const uint8_t *y; int C;
+    int B, sort_below, hist_only, bin_rule, criterion, P, cap, max_depth, n_threads;
+    int64_t big_node;
+    double lambda;
+    int32_t *cur;            /* this level's segments (partitioned in place) */
+    const orc_pending *lvl;  /* this level's nodes */
+    orc_node_res *res;       /* per node of the level */
+    int64_t m;
+    int64_t next;            /* next small node to take (guarded by mu) */
+    int failed;
+    pthread_mutex_t mu;
+} orc_level_job;
+
+/* Phase A for node j: counts, leaf tests, sampling, search, in-place stable
+ * partition.  tmp holds at least the node's sample count; the work arrays
+ * hold P (ptr P+1) and P*cap entries.  threads > 1 divides the projections. */
+static int orc_level_node(orc_level_job *L, int64_t j, int threads, int32_t *tmp, int32_t *pnnz,
+                          int32_t *pfeat, int8_t *psign, int32_t *ptr, int32_t *cfeat, int8_t *csign)
+{
+    const orc_pending nd = L->lvl[j];
+    orc_node_res *r = &L->res[j];
+    int32_t *seg = L->cur + nd.off;
+    const int C = L->C, cap = L->cap, P = L->P;
+    memset(r, 0, sizeof(*r));
+    for (int64_t i = 0; i < nd.cnt; i++)
+        r->N[L->y[seg[i]]]++;
+    int present = 0, maj = 0;
+    for (int c = 0; c < C; c++) {
+        if (r->N[c] > 0) present++;
+        if (r->N[c] > r->N[maj]) maj = c;
+    }
+    r->maj = maj;
+    r->sp.path = -1;
+    if (nd.cnt < 2 || present < 2 || (L->max_depth >= 0 && nd.depth >= L->max_depth))
+        return 0;
+    if (orc_sample_node(nd.key, P, L->d, L->lambda, cap, pnnz, pfeat, psign))
+        return -1;
+    ptr[0] = 0;
+    for (int p = 0; p < P; p++) {
+        for (int q = 0; q < pnnz[p]; q++) {
+            cfeat[ptr[p] + q] = pfeat[p * cap + q];
+            csign[ptr[p] + q] = psign[p * cap + q];
+        }
+        ptr[p + 1] = ptr[p] + pnnz[p];
+    }
+    int rc;
+    if (threads > 1)
+        rc = orc_split_search_mt(L->X, L->ld, L->y, C, seg, nd.cnt, P, ptr, cfeat, csign, L->B,
+                                 L->sort_below, L->hist_only, L->bin_rule, nd.key, L->criterion,
+                                 threads, &r->sp, NULL);
+    else
+        rc = orc_split_search_rule(L->X, L->ld, L->y, C, seg, nd.cnt, P, ptr, cfeat, csign, L->B,
+                                   L->sort_below, L->hist_only, L->bin_rule, nd.key, 0,
+                                   L->criterion, &r->sp, NULL, NULL, NULL, NULL, NULL);
+    if (rc)
+        return -1;
+    r->searched = 1;
+    if (!r->sp.valid)
+        return 0;
+    int k = pnnz[r->sp.proj];
+    const int32_t *wf = pfeat + r->sp.proj * cap;
+    const int8_t *ws = psign + r->sp.proj * cap;
+    r->k = k;
+    for (int q = 0; q < k; q++) {
+        r->feat[q] = wf[q];
+        r->sign[q] = ws[q];
+    }
+    int64_t nl = 0;
+    for (int64_t i = 0; i < nd.cnt; i++)
+        if (project(L->X, L->ld, seg[i], wf, ws, k) < r->sp.threshold)
+            tmp[nl++] = seg[i];
+    int64_t rr = nl;
+    for (int64_t i = 0; i < nd.cnt; i++)
+        if (!(project(L->X, L->ld, seg[i], wf, ws, k) < r->sp.threshold))
+            tmp[rr++] = seg[i];
+    if (nl != r->sp.n_left)
+        return -1; /* cannot happen: the split's left count is the partition's */
+    memcpy(seg, tmp, (size_t)nd.cnt * sizeof(int32_t));
+    return 0;
+}
+
+typedef struct {
+    orc_level_job *L;
+    int32_t *tmp, *pnnz, *pfeat, *ptr, *cfeat;
+    int8_t *psign, *csign;
+} orc_worker;
+
+static void *orc_level_worker(void *arg)
+{
+    orc_worker *w = (orc_worker *)arg;
+    orc_level_job *L = w->L;
+    for (;;) {
+        int64_t j = -1;
+        pthread_mutex_lock(&L->mu);
+        while (L->next < L->m && L->lvl[L->next].cnt >= L->big_node)
+            L->next++; /* large nodes were done in phase A's first part */
+        if (L->next < L->m && !L->failed)
+            j = L->next++;
+        pthread_mutex_unlock(&L->mu);
+        if (j < 0)
+            break;
+        if (orc_level_node(L, j, 1, w->tmp, w->pnnz, w->pfeat, w->psign, w->ptr, w->cfeat, w->csign)) {
+            pthread_mutex_lock(&L->mu);
+            L->failed = 1;
+            pthread_mutex_unlock(&L->mu);
+        }
+    }
+    return NULL;
+}
+
+int orc_train_tree_mt(const float *X, int64_t ld, int32_t d, const uint8_t *y, int C,
+                      const int32_t *root_idx, int64_t n_root, int B, int sort_below,
+                      int hist_only, int bin_rule, int criterion, int P, double lambda, int cap,
+                      uint64_t seed, int32_t tree_id, int32_t max_depth, int n_threads,
+                      int64_t big_node, orc_tree *out)
+{
+    memset(out, 0, sizeof(*out));
+    if (C < 1 || C > ORC_MAX_CLASSES || cap < 1 || cap > ORC_MAX_CAP || n_root < 1 || P < 1)
+        return -1;
+    if (n_threads < 1)
+        n_threads = 1;
+    out->n_classes = C;
+    out->cap = cap;
+    if (tree_reserve(out, 2 * n_root + 1, C, cap))
+        return -1;
+
+    int32_t *cur = (int32_t *)malloc((size_t)n_root * sizeof(int32_t));
+    int32_t *nxt = (int32_t *)malloc((size_t)n_root * sizeof(int32_t));
+    orc_pending *lvl = (orc_pending *)malloc((size_t)n_root * sizeof(orc_pending));
+    orc_pending *nlv = (orc_pending *)malloc((size_t)n_root * sizeof(orc_pending));
+    orc_node_res *res = NULL;
+    int64_t res_cap = 0;
+    orc_worker *wk = (orc_worker *)calloc((size_t)n_threads, sizeof(orc_worker));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    int rc = -1;
+    if (!cur || !nxt || !lvl || !nlv || !wk || !th)
+        goto done;
+    for (int t = 0; t < n_threads; t++) {
+        wk[t].tmp = (int32_t *)malloc((size_t)n_root * sizeof(int32_t));
+        wk[t].pnnz = (int32_t *)malloc((size_t)P * sizeof(int32_t));
+        wk[t].pfeat = (int32_t *)malloc((size_t)P * cap * sizeof(int32_t));
+        wk[t].psign = (int8_t *)malloc((size_t)P * cap);
+        wk[t].ptr = (int32_t *)malloc((size_t)(P + 1) * sizeof(int32_t));
+        wk[t].cfeat = (int32_t *)malloc((size_t)P * cap * sizeof(int32_t));
+        wk[t].csign = (int8_t *)malloc((size_t)P * cap);
+        if (!wk[t].tmp || !wk[t].pnnz || !wk[t].pfeat || !wk[t].psign || !wk[t].ptr ||
+            !wk[t].cfeat || !wk[t].csign)
+            goto done;
+    }
+
+    memcpy(cur, root_idx, (size_t)n_root * sizeof(int32_t));
+    int64_t m = 1, n_nodes = 1, level_base = 0;
+    lvl[0].off = 0;
+    lvl[0].cnt = n_root;
+    lvl[0].key = orc_root_key(seed, tree_id);
+    lvl[0].depth = 0;
+
+    while (m > 0) {
+        if (m > res_cap) {
+            orc_node_res *q = (orc_node_res *)realloc(res, (size_t)m * sizeof(orc_node_res));
+            if (!q)
+                goto done;
+            res = q;
+            res_cap = m;
+        }
+        orc_level_job L;
+        memset(&L, 0, sizeof(L));
+        L.X = X; L.ld = ld; L.d = d; L.y = y; L.C = C;
+        L.B = B; L.sort_below = sort_below; L.hist_only = hist_only; L.bin_rule = bin_rule;
+        L.criterion = criterion; L.P = P; L.cap = cap; L.max_depth = max_depth;
+        L.n_threads = n_threads; L.big_node = big_node; L.lambda = lambda;
+        L.cur = cur; L.lvl = lvl; L.res = res; L.m = m;
+        pthread_mutex_init(&L.mu, NULL);
+        /* phase A, large nodes: one at a time, projections over the threads */
+        int fail = 0;
+        for (int64_t j = 0; j < m && !fail; j++)
+            if (lvl[j].cnt >= big_node)
+                fail = orc_level_node(&L, j, n_threads, wk[0].tmp, wk[0].pnnz, wk[0].pfeat,
+                                      wk[0].psign, wk[0].ptr, wk[0].cfeat, wk[0].csign);
+        /* phase A, the other nodes: one per thread at a time */
+        int started = 0;
+        if (!fail) {
+            for (int t = 0; t < n_threads; t++)
+                wk[t].L = &L;
+            for (int t = 1; t < n_threads && m > 1; t++) {
+                if (pthread_create(&th[t], NULL, orc_level_worker, &wk[t]) != 0)
+                    break;
+                started = t;
+            }
+            orc_level_worker(&wk[0]);
+            for (int t = 1; t <= started; t++)
+                pthread_join(th[t], NULL);
+            fail = L.failed;
+        }
+        pthread_mutex_destroy(&L.mu);
+        if (fail)
+            goto done;
+
+        /* phase B: records and the next level, in node order */
+        int64_t m_next = 0, next_off = 0;
+        for (int64_t j = 0; j < m; j++) {
+            int64_t id = level_base + j;
+            const orc_pending nd = lvl[j];
+            const orc_node_res *r = &res[j];
+            out->left[id] = -1;
+            out->right[id] = -1;
+            out->depth[id] = nd.depth;
+            out->leaf_class[id] = r->maj;
+            out->proj_nnz[id] = 0;
+            out->cand[id] = -1;
+            out->path[id] = r->searched ? (int8_t)r->sp.path : (int8_t)-1;
+            out->threshold[id] = 0.0f;
+            out->gain[id] = 0.0;
+            out->n_samples[id] = nd.cnt;
+            for (int c = 0; c < C; c++)
+                out->class_counts[id * C + c] = r->N[c];
+            for (int q = 0; q < cap; q++) {
+                out->feat[id * cap + q] = 0;
+                out->sign[id * cap + q] = 0;
+            }
+            if (!r->searched || !r->sp.valid)
+                continue;
+            out->proj_nnz[id] = r->k;
+            for (int q = 0; q < r->k; q++) {
+                out->feat[id * cap + q] = r->feat[q];
+                out->sign[id * cap + q] = r->sign[q];
+            }
+            out->cand[id] = r->sp.cand;
+            out->threshold[id] = r->sp.threshold;
+            out->gain[id] = r->sp.gain;
+            memcpy(nxt + next_off, cur + nd.off, (size_t)nd.cnt * sizeof(int32_t));
+            int64_t nl = r->sp.n_left;
+            int64_t lid = n_nodes, rid = n_nodes + 1;
+            n_nodes += 2;
+            out->left[id] = (int32_t)lid;
+            out->right[id] = (int32_t)rid;
+            nlv[m_next].off = next_off;
+            nlv[m_next].cnt = nl;
+            nlv[m_next].key = orc_child_key(nd.key, 0);
+            nlv[m_next].depth = nd.depth + 1;
+            nlv[m_next + 1].off = next_off + nl;
+            nlv[m_next + 1].cnt = nd.cnt - nl;
+            nlv[m_next + 1].key = orc_child_key(nd.key, 1);
+            nlv[m_next + 1].depth = nd.depth + 1;
+            m_next += 2;
+            next_off += nd.cnt;
+        }
+        level_base += m;
+        m = m_next;
+        int32_t *ti = cur; cur = nxt; nxt = ti;
+        orc_pending *tl = lvl; lvl = nlv; nlv = tl;
+    }
+    out->n_nodes = n_nodes;
+    rc = 0;
+done:
+    if (wk)
+        for (int t = 0; t < n_threads; t++) {
+            free(wk[t].tmp); free(wk[t].pnnz); free(wk[t].pfeat); free(wk[t].psign);
+            free(wk[t].ptr); free(wk[t].cfeat); free(wk[t].csign);
+        }
+    free(wk); free(th); free(res);
+    free(cur); free(nxt); free(lvl); free(nlv);
+    if (rc)
+        orc_tree_free(out);
+    return rc;
+}

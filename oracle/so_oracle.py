@@ -75,6 +75,11 @@ def lib():
                                      C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
                                      C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int32,
                                      C.c_int32, C.c_void_p]
+        L.orc_train_tree_mt.restype = C.c_int
+        L.orc_train_tree_mt.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int,
+                                        C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int32,
+                                        C.c_int32, C.c_int, C.c_int64, C.c_void_p]
         L.orc_tree_free.restype = None
         L.orc_tree_free.argtypes = [C.c_void_p]
         L.orc_split_search_mt.restype = C.c_int
@@ -331,16 +336,24 @@ class Tree:
 def train_tree(X: np.ndarray, y: np.ndarray, n_classes: int, root_idx: np.ndarray, *,
                n_proj: int, lam: float, cap: int, n_bins: int = 256, sort_below: int = 1024,
                hist_only: bool = False, seed: int = 0, tree_id: int = 0,
-               max_depth: int = -1, bin_rule: int = 0, criterion: int = 0) -> Tree:
+               max_depth: int = -1, bin_rule: int = 0, criterion: int = 0,
+               n_threads: Optional[int] = None, big_node: int = 65536) -> Tree:
+    """n_threads None: orc_train_tree; an int: orc_train_tree_mt on that many
+    host threads (each level's nodes searched in parallel, nodes of at least
+    big_node samples with their projections divided over the threads; the
+    same tree)."""
     X = _c(X, np.float32)
     y = _c(y, np.uint8)
     root_idx = _c(root_idx, np.int32)
     t = OrcTree()
-    rc = lib().orc_train_tree(_p(X), X.shape[1], X.shape[0], _p(y), n_classes, _p(root_idx),
-                              root_idx.shape[0], n_bins, sort_below, int(bool(hist_only)),
-                              int(bin_rule), int(criterion), n_proj, lam, cap, C.c_uint64(seed), tree_id,
-                              max_depth,
-                              C.byref(t))
+    args = (_p(X), X.shape[1], X.shape[0], _p(y), n_classes, _p(root_idx),
+            root_idx.shape[0], n_bins, sort_below, int(bool(hist_only)),
+            int(bin_rule), int(criterion), n_proj, lam, cap, C.c_uint64(seed), tree_id,
+            max_depth)
+    if n_threads is None:
+        rc = lib().orc_train_tree(*args, C.byref(t))
+    else:
+        rc = lib().orc_train_tree_mt(*args, int(n_threads), int(big_node), C.byref(t))
     if rc:
         raise RuntimeError("orc_train_tree failed")
     try:

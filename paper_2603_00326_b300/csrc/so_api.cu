@@ -18,9 +18,10 @@
 using namespace sof;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
+namespace sof {
 so_status fail(so_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -30,6 +31,9 @@ so_status fail(so_status st, const char* fmt, ...) {
   g_err = buf;
   return st;
 }
+}  // namespace sof
+
+namespace {
 
 #define SO_CK(call)                                                                  \
   do {                                                                               \
@@ -106,6 +110,10 @@ class ArenaLease {
   bool held_ = false;
 };
 
+}  // namespace
+
+namespace sof {
+
 so_status check_dataset(const so_dataset* ds) {
   if (!ds) return fail(SO_EINVAL, "dataset is NULL");
   if (!ds->X || !ds->y) return fail(SO_EINVAL, "dataset X or y is NULL");
@@ -119,7 +127,7 @@ so_status check_dataset(const so_dataset* ds) {
 
 // keys_given: the caller supplies the random-width node keys through
 // p->bin_keys (the tree trainer and the autotuner use keys of their own).
-so_status check_params(const so_split_params* p, bool keys_given = true) {
+so_status check_params(const so_split_params* p, bool keys_given) {
   if (!p) return fail(SO_EINVAL, "params is NULL");
   if (p->n_bins < 2 || p->n_bins > kMaxBins) return fail(SO_EINVAL, "n_bins=%d outside 2..256", p->n_bins);
   if (p->sort_below < 0 || p->sort_below > kMaxSortBelow)
@@ -187,6 +195,10 @@ ProjView csr_view(const so_projs* pr) {
   return v;
 }
 
+}  // namespace sof
+
+namespace {
+
 size_t search_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, int32_t T, int32_t hist_only,
                     int32_t bin_rule) {
   Carver cv;
@@ -210,17 +222,6 @@ size_t batch_bytes(int32_t m, int64_t n_total, int32_t P, int32_t C, int32_t B, 
   return search_bytes(m, n_total, P, C, B, T, hist_only, bin_rule) + (vb ? vb * sizeof(float) + 256 : 0);
 }
 
-template <typename F>
-so_status guarded(F f) {
-  try {
-    return f();
-  } catch (const std::bad_alloc&) {
-    return fail(SO_ENOMEM, "host allocation failed");
-  } catch (...) {
-    return fail(SO_EINTERNAL, "unexpected exception");
-  }
-}
-
 }  // namespace
 
 namespace sof {
@@ -236,6 +237,7 @@ const char* so_last_error(void) { return g_err.c_str(); }
 const char* so_version(void) { return "soforest-b300 0.1 (sm_103a)"; }
 
 void so_shutdown(void) {
+  noalloc_forget();
   std::lock_guard<std::mutex> lk(g_arenas_mu);
   int cur = 0;
   cudaGetDevice(&cur);

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <new>
 #include <cuda_runtime.h>
 
 #include "../../include/soforest.h"
@@ -303,5 +304,37 @@ cudaError_t launch_tree_level(int32_t m, const Frontier cur, Frontier nxt, const
                               const int64_t* left_counts, int32_t max_depth, int64_t node_base_next,
                               TreeDev t, PartNode* pnodes, V4* tiles, V4* total, LevelStats* stats,
                               cudaStream_t st);
+
+// ---- argument checks and conventions shared by every entry point ------------
+// Sets the thread-local message of so_last_error() and returns st.
+so_status fail(so_status st, const char* fmt, ...);
+// Each returns SO_OK or SO_EINVAL with a message.  keys_given: the caller
+// supplies the random-width node keys through p->bin_keys.
+so_status check_dataset(const so_dataset* ds);
+so_status check_params(const so_split_params* p, bool keys_given = true);
+so_status check_projs(const so_projs* pr);
+// Re-score window actually used: eps raised to the float gain's error floor.
+float effective_eps(float eps, int C);
+// Longest projection row to assume (max_nnz, or the cap when unknown).
+int32_t projs_max_nnz(const so_projs* pr);
+// The histogram work decomposition a caller (or so_autotune) chose.
+void apply_tuning(SearchArgs& a, int32_t proj_per_cta, int32_t chunk);
+DatasetView view_of(const so_dataset* ds);
+ProjView csr_view(const so_projs* pr);
+// Forgets the cached device addresses of the allocation-free entry point's
+// static scratch (so_shutdown calls it; the next call looks them up again).
+void noalloc_forget();
+
+// Runs an entry point's body; no C++ exception crosses the ABI.
+template <typename F>
+so_status guarded(F f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return fail(SO_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(SO_EINTERNAL, "unexpected exception");
+  }
+}
 
 }  // namespace sof

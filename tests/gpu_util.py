@@ -78,19 +78,25 @@ def assert_split_equal(gpu, orc, ctx=""):
         assert int(g["proj"]) == -1 and int(g["cand"]) == -1, (ctx, g, orc)
 
 
-def assert_tree_equal(gt, ot):
-    assert gt.n_nodes == ot.n_nodes, (gt.n_nodes, ot.n_nodes)
-    for f in ot.FIELDS:
-        a, b = getattr(gt, f), getattr(ot, f)
-        if a.dtype.kind == "f":
-            np.testing.assert_array_equal(a.view(np.uint32 if a.itemsize == 4 else np.uint64),
-                                          b.view(np.uint32 if b.itemsize == 4 else np.uint64), err_msg=f)
-        else:
-            np.testing.assert_array_equal(a, b, err_msg=f)
-
-
 def oracle_node_projs(ptr, feat, sign, P, j):
     """CSR rows of node j out of a node-major CSR."""
     rows = ptr[j * P:(j + 1) * P + 1]
     base = int(rows[0])
     return (rows - base).astype(np.int32), feat[base:int(rows[-1])], sign[base:int(rows[-1])]
+
+
+def assert_tree_equal(gt, ot, ctx=""):
+    """Every field of two trees bit for bit; names the first differing node."""
+    assert gt.n_nodes == ot.n_nodes, (ctx, gt.n_nodes, ot.n_nodes)
+    for f in O.Tree.FIELDS:
+        a, b = np.asarray(getattr(gt, f)), np.asarray(getattr(ot, f))
+        assert a.shape == b.shape, (ctx, f)
+        bad = np.flatnonzero((a.view(np.uint8).reshape(a.shape[0], -1) !=
+                              b.view(np.uint8).reshape(b.shape[0], -1)).any(axis=1))
+        assert bad.size == 0, (ctx, f, "first differing node", int(bad[0]) if bad.size else None)
+
+
+def oracle_tree_all_cores(X, y, C, root, **kw):
+    """The oracle's tree grown on every host core (orc_train_tree_mt)."""
+    import os
+    return O.train_tree(X, y, C, root, n_threads=os.cpu_count() or 1, **kw)

@@ -170,3 +170,44 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(name, "size")] == C.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_too_small_caller_workspace_is_rejected_on_host(L):
+    """A caller workspace below the size the search needs returns SO_ENOMEM
+    before any launch, for the one-node and the batched search."""
+    from paper_2603_00326_b300 import soforest as S
+    ds = _fake_dataset()
+    pr = S.so_projs(4, 0x3000, 0x4000, 0x5000)
+    prm = S.split_params(n_bins=256, sort_below=0, hist_only=True)
+    out = S.so_split()
+    need = S.so_split_search_ws_bytes(1, 10, 4, 2, prm)
+    assert need > 1024
+    for ws in (1, need // 4):
+        st = L.so_split_search(C.byref(ds), C.c_void_p(0x6000), 10, C.byref(pr), C.byref(prm), C.byref(out),
+                               None, C.c_void_p(0x7000), ws, None)
+        assert st == S.SO_ENOMEM, st
+        assert "workspace" in S.so_last_error()
+        st = L.so_split_search_batch(C.byref(ds), C.c_void_p(0x6000), 10, C.c_void_p(0x6100), 1, C.byref(pr),
+                                     C.byref(prm), C.c_void_p(0x6200), None, C.c_void_p(0x7000), ws, None)
+        assert st == S.SO_ENOMEM, st
+        assert "workspace" in S.so_last_error()
+
+
+def test_noalloc_shares_the_argument_checks(L):
+    """The allocation-free entry point rejects what so_split_search rejects,
+    with the same messages, before touching the device."""
+    from paper_2603_00326_b300 import soforest as S
+    pr = S.so_projs(4, 0x3000, 0x4000, 0x5000)
+    out = S.so_split()
+    for ds, prm, what in ((_fake_dataset(n_classes=9), S.split_params(), "n_classes"),
+                          (_fake_dataset(), S.split_params(n_bins=257), "n_bins"),
+                          (_fake_dataset(), S.split_params(bin_rule=1), "bin_keys"),
+                          (_fake_dataset(), S.split_params(chunk=100), "chunk")):
+        st = L.so_split_search_noalloc(C.byref(ds), C.c_void_p(0x6000), 10, C.byref(pr), C.byref(prm),
+                                       C.byref(out), None, None)
+        assert st == S.SO_EINVAL
+        assert what in S.so_last_error()
+    big = S.so_projs(1024, 0x3000, 0x4000, 0x5000)
+    st = L.so_split_search_noalloc(C.byref(_fake_dataset(n_classes=8)), C.c_void_p(0x6000), 4000, C.byref(big),
+                                   C.byref(S.split_params(256, 0, True)), C.byref(out), None, None)
+    assert st == S.SO_EINVAL and "static" in S.so_last_error()

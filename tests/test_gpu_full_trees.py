@@ -1,9 +1,11 @@
-"""Whole trees at the benchmark's full sizes, checked node by node against
-the oracle (tests/tree_check.py): every node's samples, counts and children by
-routing the root samples with the oracle's projection arithmetic, and a
-spread of nodes (root, each depth band, random internal nodes, searched
-leaves) re-searched by the oracle from its own projection sampler; then the
-tree's predictions for 50,000 rows against the oracle's traversal.
+"""Whole trees at the benchmark's full sizes, identical to the oracle's.
+
+The oracle grows the same tree on every host core (orc_train_tree_mt, pinned
+to the single-threaded grower in tests/test_oracle_tree_mt.py) and the GPU
+tree must equal it field by field, bit for bit: every node's projection,
+candidate, path, threshold, FP64 gain, sample and class counts, children,
+depth and leaf class.  The tree's predictions for 50,000 rows are checked
+against the oracle's traversal too.
 
 * forest_2m: n=2M, d=256 lognormal features, 8-sparse median-centred labels
   with 10% flips, bootstrap root, 128 projections/node, T=1024, with the
@@ -20,7 +22,6 @@ import pytest
 from oracle import so_oracle as O
 from paper_2603_00326_b300 import datagen as G
 from tests import gpu_util as U
-from tests.tree_check import choose_nodes, route_and_sample
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +33,7 @@ def S():
     return soforest
 
 
-def _grow_and_check(S, ds_np, root, p, seed, tree_id, n_internal, row_major=False):
+def _grow_and_check(S, ds_np, root, p, seed, tree_id, row_major=False):
     ds = U.upload_dataset(ds_np.X, ds_np.y, ds_np.n_classes)
     if row_major:
         ds = ds.with_row_major()
@@ -44,11 +45,10 @@ def _grow_and_check(S, ds_np, root, p, seed, tree_id, n_internal, row_major=Fals
     np.testing.assert_array_equal(pred.cpu().numpy()[rows], O.predict_tree_c(gt, ds_np.X, rows))
     del ds, pred
     U.torch_cuda().cuda.empty_cache()
-    ids = choose_nodes(gt, n_internal=n_internal, n_leaves=6, seed=tree_id + 1)
-    n = route_and_sample(gt, ds_np.X, ds_np.y, ds_np.n_classes, root, n_proj=p["n_proj"], lam=p["lam"],
-                         cap=p["cap"], n_bins=p["n_bins"], sort_below=p["sort_below"], seed=seed,
-                         tree_id=tree_id, check_ids=ids)
-    assert n >= min(len(ids), 8)
+    ot = U.oracle_tree_all_cores(ds_np.X, ds_np.y, ds_np.n_classes, root, n_proj=p["n_proj"], lam=p["lam"],
+                                 cap=p["cap"], n_bins=p["n_bins"], sort_below=p["sort_below"], seed=seed,
+                                 tree_id=tree_id)
+    U.assert_tree_equal(gt, ot)
     return gt
 
 
@@ -59,7 +59,7 @@ def test_forest_2m_tree_full_size(S):
     cfg = F.ForestConfig(n_trees=p["n_trees"], n_proj=p["n_proj"], lam=p["lam"], cap=p["cap"],
                          sort_below=p["sort_below"])
     root = F.root_indices(ds_np.n, 0, cfg)
-    gt = _grow_and_check(S, ds_np, root, p, cfg.seed, 0, n_internal=16, row_major=True)
+    gt = _grow_and_check(S, ds_np, root, p, cfg.seed, 0, row_major=True)
     assert set(np.unique(gt.path)) >= {0, 1}
 
 
@@ -67,7 +67,7 @@ def test_wide_counts_tree_full_size(S):
     ds_np = G.wide_counts()
     p = G.WORKLOAD_PARAMS["wide_counts"]
     root = G.all_indices(ds_np.n)
-    gt = _grow_and_check(S, ds_np, root, p, G.PROJ_SEED_BASE + 4, 0, n_internal=16)
+    gt = _grow_and_check(S, ds_np, root, p, G.PROJ_SEED_BASE + 4, 0)
     assert set(np.unique(gt.path)) >= {0, 1}
 
 
@@ -75,5 +75,5 @@ def test_trunk_1m_tree_full_size(S):
     ds_np = G.trunk(n=1_000_000, p=1024)
     p = G.WORKLOAD_PARAMS["trunk"]
     root = G.all_indices(ds_np.n)
-    gt = _grow_and_check(S, ds_np, root, p, G.PROJ_SEED_BASE + 5, 0, n_internal=12, row_major=True)
+    gt = _grow_and_check(S, ds_np, root, p, G.PROJ_SEED_BASE + 5, 0, row_major=True)
     assert set(np.unique(gt.path)) >= {0, 1}
