@@ -155,6 +155,7 @@ struct StagedPlan {
   unsigned long long* ctr;  // next item to take (zeroed before the launch)
 };
 
+
 // Items are taken from a counter, so a CTA that drew short items takes more
 // (items differ a lot in size: chunks of large nodes and whole small ones).
 // Every item's output is order-independent (atomic min / max and histogram
@@ -291,27 +292,10 @@ __device__ __forceinline__ void build_desc(const ProjView& pv, int64_t qbase, in
 // i = tid % St and rows tid/St + k*(NT/St), one 4-byte copy per element;
 // columns past the item's end repeat its first sample (min / max unchanged;
 // their labels are marked invalid).  Nothing passes through registers.
-__device__ __forceinline__ void tile_issue(const DatasetView& ds, const int32_t* __restrict__ idx, int64_t tbeg,
-                                           int64_t tend, int St, int U, const int* s_rowfeat, bool vec,
-                                           float* dst) {
-  if (vec) {
-    const int lq = __ffs(St) - 3;  // log2(St / 4)
-    const int total = U << lq;
-    const int64_t sid0 = idx[tbeg];
-    for (int e = threadIdx.x; e < total; e += kStThreads) {
-      const int r = e >> lq, q = e & ((1 << lq) - 1);
-      cp_async16(dst + r * St + 4 * q, ds.X + (int64_t)s_rowfeat[r] * ds.ld + sid0 + 4 * q);
-    }
-  } else {
-    const int i = threadIdx.x & (St - 1);
-    const int rstep = kStThreads / St;
-    const int64_t pos = tbeg + i;
-    const int64_t sid = safe_sample(idx[pos < tend ? pos : tbeg], ds.n);
-    const float* xs = ds.X + sid;
-    for (int r = threadIdx.x / St; r < U; r += rstep) cp_async4(dst + r * St + i, xs + (int64_t)s_rowfeat[r] * ds.ld);
-  }
-}
-
+// (Tensor-map gathers of four feature rows (cp.async.bulk.tensor gather4)
+// were measured in place of the 16-byte copies: 1.91 against 1.49 ms for the
+// histogram kernel on the 4M-sample root, 0.85 against 0.67 ms for the
+// min / max kernel.)
 
 // Per-thread copy plan of an item's tiles.  Every tile of an item has the same
 // rows and width and only its first sample moves, so the thread's source and
@@ -577,9 +561,11 @@ struct ItemScanF {
 // Static assignment of an item's projections to warps, balanced by non-zero
 // count: projections ranked by k (descending, counting sort) are dealt to the
 // warps in snake order (0..31, 31..0, ...).  s_assign[w * nslot + s] is the
-// s-th projection of warp w, or -1.  Needs s_dk complete; the caller syncs
-// before reading s_assign.
-__device__ __forceinline__ int assign_snake(int np, const int* s_dk, int* s_kcnt, int* s_assign) {
+// s-th projection of warp w, or -1; s_slot (if given) is the inverse map,
+// projection -> w * nslot + s.  Needs s_dk complete; the caller syncs before
+// reading s_assign or s_slot.
+__device__ __forceinline__ int assign_snake(int np, const int* s_dk, int* s_kcnt, int* s_assign,
+                                            int* s_slot = nullptr) {
   const int nslot = (np + kStWarps - 1) / kStWarps;
   for (int e = threadIdx.x; e < kMaxCap + 1; e += kStThreads) s_kcnt[e] = 0;
   for (int e = threadIdx.x; e < nslot * kStWarps; e += kStThreads) s_assign[e] = -1;
@@ -600,6 +586,7 @@ __device__ __forceinline__ int assign_snake(int np, const int* s_dk, int* s_kcnt
     const int round = r / kStWarps, j = r - round * kStWarps;
     const int w = (round & 1) ? (kStWarps - 1 - j) : j;
     s_assign[w * nslot + round] = p;
+    if (s_slot) s_slot[p] = w * nslot + round;
   }
   return nslot;
 }
@@ -693,6 +680,64 @@ __device__ __forceinline__ void project_tile2(unsigned tile, unsigned dpk, int k
   }
 }
 
+// Straight-line form of project_tile2 for rows of at most 8 terms (row stride
+// 8 words): one warp-uniform dispatch on k picks a fully unrolled body that
+// reads the row's descriptor words in 16-byte broadcasts (one for k <= 4), so
+// no loop control runs per term.  The terms are added in row order, as
+// project_tile2 adds them.
+template <int V, int NQ, int K>
+__device__ __forceinline__ void proj_fixed(unsigned base, unsigned dpk, float2 (&acc)[V * NQ / 2]) {
+#pragma unroll
+  for (int i = 0; i < V * NQ / 2; ++i) acc[i] = make_float2(0.0f, 0.0f);
+  uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+  if (K > 0) a = lds_u4(dpk);
+  if (K > 4) b = lds_u4(dpk + 16u);
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const uint32_t w = j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : j == 3 ? a.w
+                     : j == 4 ? b.x : j == 5 ? b.y : j == 6 ? b.z : b.w;
+    const float s = desc_sign(w);
+    const float2 s2 = make_float2(s, s);
+    const unsigned row = base + (w & 0xffffu);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (V == 4) {
+        const float4 x = lds_f4(row + 512 * q);
+        acc[2 * q] = ffma2(s2, make_float2(x.x, x.y), acc[2 * q]);
+        acc[2 * q + 1] = ffma2(s2, make_float2(x.z, x.w), acc[2 * q + 1]);
+      } else {
+        acc[q] = ffma2(s2, lds_f2(row + 256 * q), acc[q]);
+      }
+    }
+  }
+}
+
+template <int V, int NQ>
+__device__ __forceinline__ void proj_lean8(unsigned tile, unsigned dpk, int k, int lane, float2 (&acc)[V * NQ / 2]) {
+  const unsigned base = tile + 4u * V * lane;
+  switch (k) {
+    case 1: proj_fixed<V, NQ, 1>(base, dpk, acc); break;
+    case 2: proj_fixed<V, NQ, 2>(base, dpk, acc); break;
+    case 3: proj_fixed<V, NQ, 3>(base, dpk, acc); break;
+    case 4: proj_fixed<V, NQ, 4>(base, dpk, acc); break;
+    case 5: proj_fixed<V, NQ, 5>(base, dpk, acc); break;
+    case 6: proj_fixed<V, NQ, 6>(base, dpk, acc); break;
+    case 7: proj_fixed<V, NQ, 7>(base, dpk, acc); break;
+    case 8: proj_fixed<V, NQ, 8>(base, dpk, acc); break;
+    default: proj_fixed<V, NQ, 0>(base, dpk, acc); break;  // an empty row projects to +0
+  }
+}
+
+// The projection of a tile: the straight-line form when rows hold at most 8
+// terms, else the loop.
+template <int V, int NQ, int KMAX>
+__device__ __forceinline__ void proj_any(unsigned tile, unsigned dpk, int k, int lane, float2 (&acc)[V * NQ / 2]) {
+  if (KMAX <= 8)
+    proj_lean8<V, NQ>(tile, dpk, k, lane, acc);
+  else
+    project_tile2<V, NQ>(tile, dpk, k, lane, acc);
+}
+
 // Label byte offsets (class * 4) of the lane's samples, in project_tile's
 // order, from the item's label bytes (0xFF marks padding and labels outside
 // [0, C); those get a very negative offset that the address clamp sends to
@@ -718,24 +763,29 @@ __device__ __forceinline__ void tile_labels(unsigned lab, int lane, int (&yo)[V 
 // The item's tile loop, one instantiation per tile width St = 32 * V * NQ
 // (the same for every warp of the CTA).  Three tile buffers: tile tt+2 is
 // copied while tile tt is evaluated, one barrier per tile.  Warp w evaluates
-// its assigned projections; per-lane running minima and maxima of each
-// projection live in shared memory (only this warp touches them).
-template <int V, int NQ>
+// its assigned projections, keeping each lane's running minima and maxima in
+// registers, and leaves them in s_pmin / s_pmax (only this warp touches its
+// rows).
+template <int V, int NQ, int KMAX>
 __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
                                         int U, bool contig, bool rowmaj, int Sp, float* s_tile, const int* s_rowfeat,
                                         const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk,
-                                        const uint32_t* s_dpk, int kmax, float* s_pmin, float* s_pmax, int lane,
+                                        const uint32_t* s_dpk, float* s_pmin, float* s_pmax, int lane,
                                         int warp, float* vbuf, int64_t n_total) {
   constexpr int St = 32 * V * NQ;
   const int ntile = (int)((it.end - it.beg + St - 1) / St);
   const int* my = s_assign + warp * nslot;
   // the lane's running minima and maxima of the warp's projections (at most
-  // kMmPPW) stay in registers over the item's tiles
+  // kMmPPW) stay in registers over the item's tiles, and so do the slots'
+  // projections and row lengths (pl | k << 16, -1: empty slot)
   float mns[kMmPPW], mxs[kMmPPW];
+  int pks[kMmPPW];
 #pragma unroll
   for (int sl = 0; sl < kMmPPW; ++sl) {
     mns[sl] = INFINITY;
     mxs[sl] = -INFINITY;
+    const int pl = sl < nslot ? my[sl] : -1;
+    pks[sl] = pl < 0 ? -1 : (pl | (s_dk[pl] << 16));
   }
   const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig, rowmaj, Sp);
   if (ntile > 0) stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
@@ -753,10 +803,10 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
     bi = bi == 2 ? 0 : bi + 1;
 #pragma unroll
     for (int sl = 0; sl < kMmPPW; ++sl) {
-      const int pl = sl < nslot ? my[sl] : -1;
-      if (pl < 0) break;
+      if (pks[sl] < 0) break;
+      const int pl = pks[sl] & 0xffff;
       float2 acc[V * NQ / 2];
-      project_tile2<V, NQ>(tile, su32(s_dpk) + 4u * pl * kmax, s_dk[pl], lane, acc);
+      proj_any<V, NQ, KMAX>(tile, su32(s_dpk) + 4u * pl * KMAX, pks[sl] >> 16, lane, acc);
 #pragma unroll
       for (int i = 0; i < V * NQ / 2; ++i) {
         mns[sl] = fminf(fminf(mns[sl], acc[i].x), acc[i].y);
@@ -780,8 +830,8 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
   }
 #pragma unroll
   for (int sl = 0; sl < kMmPPW; ++sl) {
-    const int pl = sl < nslot ? my[sl] : -1;
-    if (pl < 0) break;
+    if (pks[sl] < 0) break;
+    const int pl = pks[sl] & 0xffff;
     s_pmin[pl * 32 + lane] = mns[sl];
     s_pmax[pl * 32 + lane] = mxs[sl];
   }
@@ -793,7 +843,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
                                                             int64_t n_total) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
-  float* s_tile = reinterpret_cast<float*>(s_raw);                         // [3][kTileF]
+  float* s_tile = reinterpret_cast<float*>(s_raw);  // [3][kTileF]
   float* s_pmin = s_tile + 3 * kTileF;                                     // [kMmGroup*32]
   float* s_pmax = s_pmin + kMmGroup * 32;                                  // [kMmGroup*32]
   uint32_t* s_dpk = reinterpret_cast<uint32_t*>(s_pmax + kMmGroup * 32);   // [kMmGroup*KMAX]
@@ -834,14 +884,14 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
     __syncthreads();  // assignment and row offsets visible
     if (U <= kMmUMax) {
       if (St == 256)
-        mm_item<4, 2>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk,
-                      KMAX, s_pmin, s_pmax, lane, warp, vbuf, n_total);
+        mm_item<4, 2, KMAX>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk,
+                            s_dpk, s_pmin, s_pmax, lane, warp, vbuf, n_total);
       else if (St == 128)
-        mm_item<4, 1>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk,
-                      KMAX, s_pmin, s_pmax, lane, warp, vbuf, n_total);
+        mm_item<4, 1, KMAX>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk,
+                            s_dpk, s_pmin, s_pmax, lane, warp, vbuf, n_total);
       else
-        mm_item<2, 1>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk,
-                      KMAX, s_pmin, s_pmax, lane, warp, vbuf, n_total);
+        mm_item<2, 1, KMAX>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk,
+                            s_dpk, s_pmin, s_pmax, lane, warp, vbuf, n_total);
     } else {
       // direct path for wide groups: each warp gathers its projections' features
       for (int pl = warp; pl < it.np; pl += kStWarps) {
@@ -879,14 +929,21 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
 }
 
 // ---- k_hist_staged: class-count histograms -----------------------------------
-// 16-bit counters in shared memory, two projections per 32-bit word: the pair
-// (2i, 2i+1) shares a [B+1][C] array of words (one spare bin), projection 2i
-// in the low half, 2i+1 in the high half; then a trash word.  A warp's atomic
-// add touches one half only, so lanes of one instruction collide only on the
-// same (bin, class).  An item holds at most 65535 samples, so no counter
-// overflows.  Addresses are byte offsets clamped (as unsigned) to the trash
-// word, which absorbs padding positions (label offset very negative), labels
-// outside [0, C) and non-finite projected values.
+// 16-bit counters in shared memory, two counter slots per 32-bit word: slots
+// (2i, 2i+1) share a [B+1][C] array of words (one spare bin), slot 2i in the
+// low half, 2i+1 in the high half; then a trash word.  A projection's slot is
+// its place in the warp assignment (warp w's s-th projection takes slot
+// w * nslot + s), so when a warp holds two projections they share one word
+// array and one base address.  A warp's atomic add touches one half only, so
+// lanes of one instruction collide only on the same (bin, class).  An item
+// holds at most 65535 samples, so no counter overflows.  Addresses are byte
+// offsets clamped (as unsigned) to the trash word, which absorbs padding
+// positions (label offset very negative), labels outside [0, C) and
+// non-finite projected values.
+// Counter word arrays of a group of PG projections: more than 32 projections
+// take two slots per warp (slots up to 63), at most 32 one slot per warp.
+__host__ __device__ __forceinline__ int hist_pairs(int PG) { return PG > kStWarps ? kStWarps : (PG + 1) >> 1; }
+
 struct BinParams {
   float mn, W, inv_w, c;
   unsigned hb;   // byte base of the projection pair's words minus magic*C*4 (mod 2^32)
@@ -946,6 +1003,48 @@ __device__ __forceinline__ void hist_tile_fast(unsigned tile, unsigned yo_tile, 
   }
 }
 
+// hist_tile_fast for the NS (1 or 2) projections a warp holds, sharing the
+// tile's label offsets and their counter base (a warp's two projections take
+// the two halves of one word array), with the straight-line projection for
+// rows of at most 8 terms.
+template <int V, int NQ, int KMAX, int NS>
+__device__ __forceinline__ void hist_tile_warp(unsigned tile, unsigned yo_tile, unsigned dpk0, unsigned dpk1, int k0,
+                                               int k1, int lane, const BinParams& b0, const BinParams& b1,
+                                               unsigned C4, unsigned limit) {
+  unsigned hy[V * NQ];
+  {
+    int yo[V * NQ];
+    tile_offsets<V, NQ>(yo_tile, lane, yo);
+#pragma unroll
+    for (int i = 0; i < V * NQ; ++i) hy[i] = b0.hb + (unsigned)yo[i];
+  }
+  const float2 m2 = make_float2(kMagic, kMagic);
+  const float2 m1 = make_float2(1.0f - kMagic, 1.0f - kMagic);
+#pragma unroll
+  for (int sp = 0; sp < NS; ++sp) {
+    const BinParams& bp = sp ? b1 : b0;
+    float2 acc[V * NQ / 2];
+    proj_any<V, NQ, KMAX>(tile, sp ? dpk1 : dpk0, sp ? k1 : k0, lane, acc);
+    const float2 inv2 = make_float2(bp.inv_w, bp.inv_w);
+    const float2 c2 = make_float2(bp.c, bp.c);
+#pragma unroll
+    for (int i = 0; i < V * NQ / 2; ++i) {
+      // the bin rule of hist_tile_fast
+      const float2 e = ffma2(acc[i], inv2, c2);
+      const float2 tq = fadd2(e, m2);
+      const float2 q1 = fadd2(tq, m1);
+      const float tbx = __fadd_rn(bp.mn, __fmul_rn(q1.x, bp.W));
+      const float tby = __fadd_rn(bp.mn, __fmul_rn(q1.y, bp.W));
+      unsigned ax = __float_as_uint(tq.x) * C4 + hy[2 * i];
+      unsigned ay = __float_as_uint(tq.y) * C4 + hy[2 * i + 1];
+      if (tbx <= acc[i].x) ax += C4;
+      if (tby <= acc[i].y) ay += C4;
+      reds_add(min(ax, limit), bp.inc);
+      reds_add(min(ay, limit), bp.inc);
+    }
+  }
+}
+
 // exact estimate-and-correct rule for projections outside the fast condition
 template <int V, int NQ>
 __device__ __forceinline__ void hist_tile_slow(unsigned tile, unsigned yo_tile, unsigned dpk, int k, int lane,
@@ -983,7 +1082,7 @@ __device__ __forceinline__ void hist_tile_rw(unsigned tile, unsigned yo_tile, un
 // one barrier per tile; labels go through a register one tile ahead.  Warp w
 // evaluates its assigned projections (at most kHistPPW) with their bin
 // parameters in registers.
-template <int V, int NQ, bool RW>
+template <int V, int NQ, bool RW, int KMAX>
 __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
                                           int U, bool contig, float* s_tile, const uint8_t* s_lab, int* s_yo,
                                           const int* s_rowfeat,
@@ -1009,6 +1108,11 @@ __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* 
     bps[sl] = BinParams{bf.x, bf.y, bf.z, bf.w, su32(s_hist) + (unsigned)bi.x, (unsigned)bi.y, bi.z};
   }
   const unsigned limit_abs = su32(s_hist) + limit;
+  // every projection of the warp on the fast equal-width rule: one pass per
+  // tile over both (shared label offsets and counter base)
+  const int nps = (pls[0] >= 0 ? 1 : 0) + (kHistPPW > 1 && pls[kHistPPW - 1] >= 0 ? 1 : 0);
+  const bool warp_fast = !RW && (pls[0] < 0 || bps[0].fast) && (kHistPPW < 2 || pls[kHistPPW - 1] < 0 ||
+                                                                   bps[kHistPPW - 1].fast);
   const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig);
   // label byte offsets of tile t into s_yo[t % 3], written with tile t's copies
   auto tile_yo = [&](int t, int b) {
@@ -1038,20 +1142,31 @@ __device__ __forceinline__ void hist_item(const DatasetView& ds, const int32_t* 
     bc = bn;
     bn = bi;
     bi = bi == 2 ? 0 : bi + 1;
+    if (warp_fast) {
+      const unsigned d0 = su32(s_dpk) + 4u * (pls[0] >= 0 ? pls[0] : 0) * kmax;
+      const unsigned d1 = su32(s_dpk) + 4u * (pls[kHistPPW - 1] >= 0 ? pls[kHistPPW - 1] : 0) * kmax;
+      if (nps == 2)
+        hist_tile_warp<V, NQ, KMAX, 2>(tile, lab, d0, d1, ks[0], ks[kHistPPW - 1], lane, bps[0], bps[kHistPPW - 1],
+                                       C4, limit_abs);
+      else if (nps == 1)
+        hist_tile_warp<V, NQ, KMAX, 1>(tile, lab, d0, d1, ks[0], ks[0], lane, bps[0], bps[0], C4, limit_abs);
+    } else {
 #pragma unroll
-    for (int sl = 0; sl < kHistPPW; ++sl) {
-      if (pls[sl] >= 0) {
-        const unsigned dpk = su32(s_dpk) + 4u * pls[sl] * kmax;
-        if (RW) {
-          const unsigned tb = rwt + 4u * kRwRow * pls[sl], gb = rwg + 2u * kRwRow * pls[sl];
-          if (bps[sl].fast)
-            hist_tile_rw<V, NQ, true>(tile, lab, dpk, ks[sl], lane, bps[sl], tb, gb, B - 1, C4, limit_abs);
-          else
-            hist_tile_rw<V, NQ, false>(tile, lab, dpk, ks[sl], lane, bps[sl], tb, gb, B - 1, C4, limit_abs);
-        } else if (bps[sl].fast) {
-          hist_tile_fast<V, NQ>(tile, lab, dpk, ks[sl], lane, bps[sl], C4, limit_abs);
-        } else {
-          hist_tile_slow<V, NQ>(tile, lab, dpk, ks[sl], lane, bps[sl], B, C, (pls[sl] >> 1) * HS, s_hist);
+      for (int sl = 0; sl < kHistPPW; ++sl) {
+        if (pls[sl] >= 0) {
+          const unsigned dpk = su32(s_dpk) + 4u * pls[sl] * kmax;
+          if (RW) {
+            const unsigned tb = rwt + 4u * kRwRow * pls[sl], gb = rwg + 2u * kRwRow * pls[sl];
+            if (bps[sl].fast)
+              hist_tile_rw<V, NQ, true>(tile, lab, dpk, ks[sl], lane, bps[sl], tb, gb, B - 1, C4, limit_abs);
+            else
+              hist_tile_rw<V, NQ, false>(tile, lab, dpk, ks[sl], lane, bps[sl], tb, gb, B - 1, C4, limit_abs);
+          } else if (bps[sl].fast) {
+            hist_tile_fast<V, NQ>(tile, lab, dpk, ks[sl], lane, bps[sl], C4, limit_abs);
+          } else {
+            hist_tile_slow<V, NQ>(tile, lab, dpk, ks[sl], lane, bps[sl], B, C, ((warp * nslot + sl) >> 1) * HS,
+                                  s_hist);
+          }
         }
       }
     }
@@ -1110,7 +1225,7 @@ __device__ __forceinline__ void hist_item_buf(const float* __restrict__ vbuf, in
           reds_add(min(a, limit_abs), bp.inc);
         }
       } else {
-        const int wbase = (pl >> 1) * HS;
+        const int wbase = ((warp * nslot + sl) >> 1) * HS;
 #pragma unroll
         for (int i = 0; i < 16; ++i)
           if (yo[i] >= 0) atomicAdd(&s_hist[wbase + bin_of(v[i], bp.mn, bp.W, bp.inv_w, B) * C + (yo[i] >> 2)], bp.inc);
@@ -1128,11 +1243,11 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
   const int C = ds.C;
-  const int HS = (B + 1) * C;  // words per projection pair
-  const int npair = (PG + 1) >> 1;
+  const int HS = (B + 1) * C;  // words per counter pair
+  const int npair = hist_pairs(PG);
   const int hist_words = (npair * HS + 1 + 3) & ~3;
   // every region starts on a 16-byte boundary
-  float* s_tile = reinterpret_cast<float*>(s_raw);                           // [3][kTileF]
+  float* s_tile = reinterpret_cast<float*>(s_raw);  // [3][kTileF]
   uint8_t* s_lab = reinterpret_cast<uint8_t*>(s_tile + 3 * kTileF);          // [kMaxItem + 512] item labels
   int* s_yo = reinterpret_cast<int*>(s_lab + kMaxItem + 512);                // [3][256] tile label offsets
   uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_yo + 3 * 256);            // [hist_words]
@@ -1149,6 +1264,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
   int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                         // [nw]
   __shared__ float4 s_bpf[kHistPGMax];  // min, W, 1/W, c
   __shared__ int4 s_bpi[kHistPGMax];    // hb, inc, fast
+  __shared__ int s_slot[kHistPGMax];    // counter slot of each projection
   __shared__ int s_misc[kStWarps + 1];
   __shared__ int s_kcnt[kMaxCap + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1187,7 +1303,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         const int pl = threadIdx.x;
         const float2 so = rw.so[it.h * P + it.p0 + pl];
         s_bpf[pl] = make_float4(so.x, so.y, 0.0f, 0.0f);
-        s_bpi[pl] = make_int4((pl >> 1) * HS * 4, (int)(1u << (16 * (pl & 1))), so.x >= 0.0f ? 1 : 0, 0);
+        s_bpi[pl] = make_int4(0, 0, so.x >= 0.0f ? 1 : 0, 0);  // counter base and increment: below
       }
     } else if (threadIdx.x < it.np) {
       const int pl = threadIdx.x;
@@ -1199,12 +1315,21 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
       const float M = fmaxf(fabsf(mn), fabsf(mx));
       const int fast = (W > 0.0f && isfinite(inv_w) && isfinite(c) && M <= kCondLimit * W) ? 1 : 0;
       s_bpf[pl] = make_float4(mn, W, inv_w, c);
-      s_bpi[pl] = make_int4((int)((unsigned)((pl >> 1) * HS * 4) - magic_bits * C4), (int)(1u << (16 * (pl & 1))),
-                            fast, 0);
+      s_bpi[pl] = make_int4(0, 0, fast, 0);  // counter base and increment: below
     }
     __syncthreads();  // s_dk and s_rowfeat complete
     for (int r = threadIdx.x; r < U && r < kStUMax; r += kStThreads) s_rowoff[r] = (int64_t)s_rowfeat[r] * ds.ld;
-    const int nslot = assign_snake(it.np, s_dk, s_kcnt, s_assign);
+    const int nslot = assign_snake(it.np, s_dk, s_kcnt, s_assign, s_slot);
+    __syncthreads();  // s_slot complete
+    if (threadIdx.x < it.np) {
+      // the projection's counters: word array of its slot pair, its half;
+      // the fast equal-width rule adds the bin estimate's rounding shift
+      // (magic * C4) to the base, so it is taken off here
+      const int pl = threadIdx.x, sl = s_slot[pl];
+      const unsigned base = (unsigned)((sl >> 1) * HS * 4);
+      s_bpi[pl].x = (int)((RW || !s_bpi[pl].z) ? base : base - magic_bits * C4);
+      s_bpi[pl].y = (int)(1u << (16 * (sl & 1)));
+    }
     const bool contig = vbuf ? false : item_contiguous(ds, idx, it.beg, it.end);  // includes a barrier
     if (vbuf || U <= kStUMax) {
       // the item's labels as bytes (0xFF: padding or outside [0, C)); read
@@ -1224,13 +1349,13 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         hist_item_buf<RW>(vbuf, n_total, it, su32(s_lab), s_assign, nslot, s_bpf, s_bpi, B, C, HS, C4,
                           su32(s_hist) + limit, s_hist, rwt, rwg, lane, warp);
       } else if (St == 256)
-        hist_item<4, 2, RW>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
+        hist_item<4, 2, RW, KMAX>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
                             s_bpf, s_bpi, B, HS, C4, limit, s_hist, rwt, rwg, lane, warp);
       else if (St == 128)
-        hist_item<4, 1, RW>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
+        hist_item<4, 1, RW, KMAX>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
                             s_bpf, s_bpi, B, HS, C4, limit, s_hist, rwt, rwg, lane, warp);
       else
-        hist_item<2, 1, RW>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
+        hist_item<2, 1, RW, KMAX>(ds, idx, it, U, contig, s_tile, s_lab, s_yo, s_rowfeat, s_rowoff, s_assign, nslot, s_dk, s_dpk, KMAX,
                             s_bpf, s_bpi, B, HS, C4, limit, s_hist, rwt, rwg, lane, warp);
     } else {
       // direct path for wide groups (rare): one warp per projection, gathers
@@ -1240,7 +1365,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
         int k = pv.end[q] - rb;
         k = k < 0 ? 0 : (k > kMaxCap ? kMaxCap : k);
         const float4 bf = s_bpf[pl];
-        const unsigned inc = 1u << (16 * (pl & 1));
+        const int slot = s_slot[pl];
+        const unsigned inc = 1u << (16 * (slot & 1));
         for (int64_t e = it.beg + lane; e < it.end; e += 32) {
           const int64_t s = safe_sample(idx[e], ds.n);
           float acc = 0.0f;
@@ -1259,7 +1385,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
           } else {
             b = bin_of(acc, bf.x, bf.y, bf.z, B);
           }
-          if (yv < C) atomicAdd(&s_hist[(pl >> 1) * HS + b * C + yv], inc);
+          if (yv < C) atomicAdd(&s_hist[(slot >> 1) * HS + b * C + yv], inc);
         }
       }
     }
@@ -1268,8 +1394,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_hist_staged(DatasetView ds, c
     const int BC = B * C;
     for (int pl = warp; pl < it.np; pl += kStWarps) {
       int32_t* g = hist + (it.h * P + it.p0 + pl) * (int64_t)BC;
-      const uint32_t* h = s_hist + (pl >> 1) * HS;
-      const int sh = 16 * (pl & 1);
+      const int slot = s_slot[pl];
+      const uint32_t* h = s_hist + (slot >> 1) * HS;
+      const int sh = 16 * (slot & 1);
       for (int r = lane; r < BC; r += 32) {
         int v = (int)((h[r] >> sh) & 0xffffu);
         if (r >= BC - C) v += (int)((h[r + C] >> sh) & 0xffffu);
@@ -1302,7 +1429,7 @@ size_t mm_smem_bytes(int /*d*/, int kmax) {
          kStUMax * 12;
 }
 size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG, bool rw) {
-  const int npair = (PG + 1) >> 1;
+  const int npair = hist_pairs(PG);
   const size_t hist_words = ((size_t)npair * (B + 1) * C + 1 + 3) & ~(size_t)3;
   const size_t rw_bytes = rw ? (size_t)PG * kRwRow * 6 : 0;
   return (size_t)3 * kTileF * 4 + kMaxItem + 512 + 3 * 256 * 4 + hist_words * 4 + rw_bytes +
