@@ -134,6 +134,79 @@ def cpu_baseline(ds, pr, n_sample_proj: int, threads: int = 1):
     return ds.n * n_sample_proj / dt, dt
 
 
+def profile_summary(name):
+    """The committed ncu summary profiles/<name>.json of a kernel, if it was
+    taken on the kernel source this run executes (the sha256 of the source
+    file it names matches); otherwise None, so that counters of an older
+    kernel are never reported as this one's."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", name + ".json")) as fh:
+            rec = json.load(fh)
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != rec["source_sha256"]:
+                return None
+        return rec
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def roofline_block(achieved, hbm, peak_kind, alg_bytes, k_avg_ms, clk):
+    """The histogram kernel against the measured HBM copy bandwidth, with its
+    DRAM traffic and its two on-chip ceilings from the committed ncu summary
+    of the same kernel source: the shared-memory pipe (one 128-byte wavefront
+    per SM per clock) and instruction issue (four warp-instructions per SM per
+    clock), each as the time that many wavefronts or instructions need at the
+    SM clock sampled during this run, over the measured launch time."""
+    out = {"bound": "hbm", "kernel": "k_hist", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+           "frac": (achieved / hbm) if achieved else None, "traffic": None, "peak_source": peak_kind,
+           "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": k_avg_ms}
+    rec = profile_summary("k_hist_staged_root_4m")
+    if rec is None or not k_avg_ms:
+        out["traffic_note"] = "no ncu summary of this kernel source under profiles/"
+        return out
+    out["traffic"] = rec["dram_bytes_per_launch"]
+    mhz = (clk or {}).get("sm_mhz") or 2032.0
+    sms = rec.get("sms", 148)
+    per_ms = sms * mhz * 1e3  # SM-clocks per millisecond
+    sram_ms = rec["shared_wavefronts_per_launch"] / per_ms
+    issue_ms = rec["warp_instructions_per_launch"] / (4 * per_ms)
+    out["ceilings"] = {
+        "shared_pipe": {"wavefronts_per_launch": rec["shared_wavefronts_per_launch"], "floor_ms": sram_ms,
+                        "frac": sram_ms / k_avg_ms},
+        "issue": {"warp_instructions_per_launch": rec["warp_instructions_per_launch"], "floor_ms": issue_ms,
+                  "frac": issue_ms / k_avg_ms},
+        "source": rec.get("summary", "profiles/k_hist_staged_root_4m.md")}
+    return out
+
+
+def gain_error(S, torch, ds, ds_np, pr, idx, off, n_proj=8):
+    """Largest relative error of the GPU's float Gini gains against the
+    oracle's double gains, over every candidate of positive double gain, for
+    the first n_proj projections of the benchmark node: the oracle's
+    per-candidate gains beside the float gains the GPU's histogram stage
+    exports (which lack the constant 1/n^2 factor: n^2 is a power of two here,
+    so the division is exact)."""
+    import oracle as O
+    from paper_2603_00326_b300 import datagen as G
+    ptr = np.ascontiguousarray(pr.ptr[:n_proj + 1])
+    r = O.split_search(ds_np.X, ds_np.y, ds_np.n_classes, G.all_indices(ds_np.n), ptr, pr.feat, pr.sign,
+                       hist_only=True, want_debug=True)
+    dev = idx.device
+    pj = S.DeviceProjs(n_proj, torch.from_numpy(ptr).to(dev), torch.from_numpy(pr.feat).to(dev),
+                       torch.from_numpy(pr.sign).to(dev), int(np.diff(ptr).max()))
+    _, _, g32 = S.so_histograms(ds, idx, off, pj, 256, want_gains=True)
+    g32 = g32.cpu().numpy()[0].astype(np.float64) / (float(ds_np.n) ** 2)
+    g64 = r.gains
+    pos = g64 > 0
+    rel = np.abs(g32[pos] - g64[pos]) / g64[pos]
+    return {"max_rel": float(rel.max()), "candidates": int(pos.sum()), "projections": n_proj,
+            "bound_stated": 1e-6,
+            "what": "max |gain32 - gain64| / gain64 over candidates with gain64 > 0 (float Gini key of the "
+                    "histogram stage against the oracle's double gain); the chosen split's gain is the double "
+                    "re-score itself"}
+
+
 def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=True):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
@@ -588,14 +661,13 @@ def run_ours(args):
 
     e2e_serial_s = e2e_run(False)
     e2e_s = e2e_run(True)
-    out_h = outs_h[(e2e_steps - 1) % 2] if e2e_steps else out_h
+    if e2e_steps:
+        out_h = outs_h[(e2e_steps - 1) % 2]
+    else:
+        out_h.copy_(out)  # the device-timed steps' split record
     rec = S.SPLIT_DTYPE and np.frombuffer(out_h.numpy().tobytes(), dtype=S.SPLIT_DTYPE)[0]
 
     # ---- roofline of the dominant kernel (histogram fill)
-    # DRAM bytes (read + write) of one k_hist_staged launch on this workload, the mean of five
-    # launches in the ncu capture summarised in profiles/kernels_dram_root_4m.md; set to None
-    # whenever that kernel changes.
-    K_HIST_TRAFFIC_BYTES = 1_099_972_556 + 4_253_491
     hbm, peak_kind = peaks()
     used_feats = np.unique(pr.feat).size
     alg_bytes = used_feats * n * 4 + n * 4 + n * 1  # feature columns + index list + labels, one pass
@@ -616,13 +688,7 @@ def run_ours(args):
                 "pipelined": "step i+1's host-to-device copies overlap step i's kernels (two device input sets)",
                 "serial_value": (world * n * P / e2e_serial_s) if e2e_steps else None},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "k_hist", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None,
-                     "traffic": K_HIST_TRAFFIC_BYTES if WORKLOAD == "root_4m" else None,
-                     "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                     "avg_launch_ms": k_avg_ms,
-                     "limit": "shared-memory atomics, shared-memory latency and instruction issue, not HBM "
-                              "(ncu: issue 66% busy, shared-memory pipe 63%, DRAM 9% of peak)"},
+        "roofline": roofline_block(achieved, hbm, peak_kind, alg_bytes, k_avg_ms, clk),
         "stage_ms_per_launch": stage_ms,
         "clocks": clk,
         "split": {"proj": int(rec["proj"]), "cand": int(rec["cand"]), "gain": float(rec["gain"]),
@@ -639,10 +705,16 @@ def run_ours(args):
         cores = host_cores()
         n_cpu = min(P, 8 * cores)
         v, dt = cpu_baseline(ds_np, pr, n_cpu, cores)
+        n_one = 4
+        v1, dt1 = cpu_baseline(ds_np, pr, n_one, 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"oracle split search (projections divided over {cores} threads) + "
                                           f"partition on all {n} samples, first {n_cpu} of {P} projections "
-                                          f"({dt:.1f} s)"}
+                                          f"({dt:.1f} s)",
+                                "value_1thread": v1,
+                                "sample_1thread": f"the same on one thread, first {n_one} of {P} projections "
+                                                  f"({dt1:.1f} s)"}
+        line["gain_error"] = gain_error(S, torch, ds, ds_np, pr, idx, off)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
