@@ -54,9 +54,11 @@ def dist_env():
     return rank, world, local
 
 
-def make_inputs():
+def make_inputs(n=None):
+    """The root node's inputs; n: a smaller node of the same recipe (profiling
+    cases), default the benchmark's 4M samples."""
     from paper_2603_00326_b300 import datagen as G
-    ds = G.root_4m()
+    ds = G.root_4m() if n is None else G.root_4m(n=n)
     p = G.WORKLOAD_PARAMS[WORKLOAD]
     rng = np.random.default_rng(G.PROJ_SEED_BASE + 1)
     pr = G.random_projections(rng, p["n_proj"], ds.d, p["lam"], p["cap"])
@@ -207,7 +209,8 @@ def gain_error(S, torch, ds, ds_np, pr, idx, off, n_proj=8):
                     "re-score itself"}
 
 
-def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=True):
+def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=True, batched_only=False,
+               wide_n=None):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
     64 projections/node, crossover T autotuned), one tree grown to purity
@@ -215,7 +218,7 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=T
     from paper_2603_00326_b300 import datagen as G
     out = {}
     if only not in (None, "frontier"):
-        return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees, rw_tree=rw_tree)
+        return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees, rw_tree=rw_tree, wide_n=wide_n)
     ds_np = G.frontier_1m()
     p = G.WORKLOAD_PARAMS["frontier_1m"]
     idx_np, off_np = G.frontier_nodes(ds_np.n, p["n_nodes"])
@@ -250,6 +253,10 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=T
         S.so_split_search_batch(dd, idx, off, pj, prm, out=outb, workspace=ws)
     torch.cuda.synchronize()
     batched_ms = (time.perf_counter() - t0) * 1000.0 / reps
+    sp = float(ds_np.n * P)
+    if batched_only:
+        return {"frontier_1m": {"nodes": m, "autotuned_sort_below": int(prm.sort_below), "batched_ms": batched_ms,
+                                "batched_sample_projections_per_s": sp / (batched_ms / 1000.0)}}
     # node-at-a-time: one synchronous call per node (the paper's offload form)
     views = []
     for j in range(m):
@@ -270,7 +277,6 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=T
     rec = S.splits_to_numpy(outb)
     same = all(int(rec[j]["proj"]) == plain[j].proj and int(rec[j]["cand"]) == plain[j].cand and
                float(rec[j]["gain"]) == plain[j].gain for j in range(m))
-    sp = float(ds_np.n * P)
     out["frontier_1m"] = {"nodes": m, "autotuned_sort_below": int(prm.sort_below),
                           "autotuned_proj_per_cta": int(prm.proj_per_cta), "autotuned_chunk": int(prm.chunk),
                           "batched_ms": batched_ms, "plain_ms": plain_ms,
@@ -279,10 +285,10 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=T
     del dd, idx, off, ws, outb, views
     if only == "frontier":
         return out
-    return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees, rw_tree=rw_tree)
+    return _later_legs(S, torch, dev, forest_trees, only, out, wide_trees, rw_tree=rw_tree, wide_n=wide_n)
 
 
-def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_trees=1, rw_tree=True):
+def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_trees=1, rw_tree=True, wide_n=None):
     from paper_2603_00326_b300 import datagen as G
     if only in (None, "tree"):
         # one tree to purity
@@ -366,7 +372,7 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
         del dd, trees, fo
     if wide_trees > 0 and only in (None, "wide"):
         # wide count-like data: n=500k, d=4096, 90% zeros, 5 classes, grown to purity
-        ws_np = G.wide_counts()
+        ws_np = G.wide_counts() if wide_n is None else G.wide_counts(n=wide_n)
         wp = G.WORKLOAD_PARAMS["wide_counts"]
         dd = S.DeviceDataset(torch.from_numpy(ws_np.X).to(dev), torch.from_numpy(ws_np.y).to(dev), 5)
         root = torch.from_numpy(G.all_indices(ws_np.n)).to(dev)
@@ -380,7 +386,7 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
             tr = S.so_train_tree(dd, root, prm)
             times.append(time.perf_counter() - t0)
         out["wide_counts"] = {"train_s": min(times), "trees": wide_trees, "nodes": tr.n_nodes,
-                              "depth": int(tr.depth.max())}
+                              "depth": int(tr.depth.max()), "n": ws_np.n}
         del dd, root
     if trunk_trees > 0 and only in (None, "trunk"):
         # the Trunk generator at the paper's 100k and 1M rows, p = 1024: one
@@ -401,8 +407,39 @@ def _later_legs(S, torch, dev, forest_trees, only, out, wide_trees=1, trunk_tree
                                              "depth": int(tr.depth.max())}
             del dd, root, tk
         out["trunk_p1024"] = res
+    if only == "trunk10m":
+        out["trunk_10m_p1024"] = trunk_10m_tree(S, torch, dev)
     torch.cuda.empty_cache()
     return out
+
+
+def trunk_10m_tree(S, torch, dev, n=10_000_000, p=1024):
+    """One tree to purity on Trunk at the paper's largest Trunk size (Table 3:
+    10M rows; p = 1024 here), 48 projections per node of 1+Poisson(1)
+    non-zeros, T = 1024, with the row-major copy.  The 41 GB feature matrix
+    is generated in 64-feature blocks straight into device memory."""
+    from paper_2603_00326_b300 import datagen as G
+    tp_ = G.WORKLOAD_PARAMS["trunk"]
+    t0 = time.perf_counter()
+    X = torch.empty((p, n), dtype=torch.float32, device=dev)
+
+    def fill(f0, blk):
+        X[f0:f0 + blk.shape[0]].copy_(torch.from_numpy(blk))
+
+    y = G.trunk_streamed(n, p, fill)
+    gen_s = time.perf_counter() - t0
+    dd = S.DeviceDataset(X, torch.from_numpy(y).to(dev), 2).with_row_major()
+    root = torch.arange(n, dtype=torch.int32, device=dev)
+    prm = S.tree_params(tp_["n_proj"], tp_["lam"], tp_["cap"], tp_["n_bins"], tp_["sort_below"],
+                        seed=G.PROJ_SEED_BASE + 5)
+    S.so_train_tree(dd, root, S.tree_params(8, 1.0, 8, 256, 1024, seed=1, max_depth=3))  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr = S.so_train_tree(dd, root, prm)
+    train_s = time.perf_counter() - t0
+    del dd, root, X
+    return {"train_s": train_s, "nodes": tr.n_nodes, "depth": int(tr.depth.max()), "n": n, "p": p,
+            "generate_s": gen_s, "device_gb": 2 * n * p * 4 / 1e9}
 
 
 def variant_step(S, torch, ds, pj, idx, off, n, P, C, n_bins, steps, key=None, criterion=0):
@@ -472,7 +509,8 @@ def run_leg(args):
     # the forest leg alone grows only the equal-width Gini trees (the variant
     # trees run in the default extras and in --leg rw)
     out = extra_legs(S, torch, dev, args.forest_trees if args.leg == "forest" else 0, only=args.leg,
-                     wide_trees=args.wide_trees if args.leg == "wide" else 0, rw_tree=False)
+                     wide_trees=args.wide_trees if args.leg == "wide" else 0, rw_tree=False,
+                     batched_only=args.batched_only, wide_n=args.wide_n)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
     return 0
 
@@ -540,7 +578,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     S.lib()
 
-    ds_np, pr, p = make_inputs()
+    ds_np, pr, p = make_inputs(args.root_n)
     n, d, P, C = ds_np.n, ds_np.d, p["n_proj"], ds_np.n_classes
     Xh = torch.from_numpy(ds_np.X).pin_memory()
     yh = torch.from_numpy(ds_np.y).pin_memory()
@@ -680,7 +718,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "d": d, "n_proj": P, "n_bins": p["n_bins"], "classes": C,
+        "config": {"workload": WORKLOAD if args.root_n is None else f"root node of {n} samples (profiling case)",
+                   "n": n, "d": d, "n_proj": P, "n_bins": p["n_bins"], "classes": C,
                    "path": "histogram", "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs {X.numel() * 4 / 1e9:.2f} GB > 126 MB L2; no flush needed"},
         "e2e": {"value": (world * n * P / e2e_s) if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -732,12 +771,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-extras", action="store_true", help="skip the frontier, tree and forest legs")
-    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest", "wide", "trunk", "rw"],
+    ap.add_argument("--leg", default=None, choices=["frontier", "tree", "forest", "wide", "trunk", "trunk10m", "rw"],
                     help="run one secondary leg alone and print its JSON")
     ap.add_argument("--forest-trees", type=int, default=2,
                     help="trees of the n=2M, d=256 forest timed in the extras (0 skips)")
     ap.add_argument("--wide-trees", type=int, default=1,
                     help="timed trees of the n=500k, d=4096 wide count-like workload (0 skips)")
+    ap.add_argument("--root-n", type=int, default=None,
+                    help="profiling case: the root step on a node of this many samples (same recipe); "
+                         "the printed line then describes that smaller node")
+    ap.add_argument("--wide-n", type=int, default=None,
+                    help="profiling case: the wide tree on this many samples (same recipe)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="frontier leg: time the batched search only (no node-at-a-time loop)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -240,6 +240,38 @@ def trunk(n: int = 1_000_000, p: int = 1024, seed: int = DATA_SEED_BASE + 5) -> 
     return Dataset(X, y, 2, "trunk")
 
 
+def trunk_streamed(n: int, p: int, fill_block, seed: int = DATA_SEED_BASE + 5, workers: int = 4):
+    """The Trunk dataset of trunk(n, p, seed), value for value, handed over in
+    64-feature blocks instead of one host array (for sizes whose matrix does
+    not fit in host memory): fill_block(f0, block) receives rows f0..f0+63 as
+    a float32 [rows, n] array, at most `workers` blocks alive at a time.
+    Returns the labels."""
+    from concurrent.futures import ThreadPoolExecutor
+    root = np.random.SeedSequence(seed)
+    children = root.spawn((p + 63) // 64 + 1)
+    y = np.zeros(n, dtype=np.uint8)
+    y[n // 2:] = 1
+    np.random.default_rng(children[-1]).shuffle(y)
+    sgn = np.where(y == 0, np.float32(1.0), np.float32(-1.0)).astype(np.float32)
+
+    def one(a):
+        f0, ss = a
+        f1 = min(p, f0 + 64)
+        blk = np.empty((f1 - f0, n), dtype=np.float32)
+        rng = np.random.default_rng(ss)
+        for f in range(f0, f1):
+            mu = np.float32(1.0 / np.sqrt(f + 1.0))
+            blk[f - f0] = rng.standard_normal(n, dtype=np.float32) + sgn * mu
+        return f0, blk
+
+    starts = list(range(0, p, 64))
+    with ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
+        for i in range(0, len(starts), workers):
+            for f0, blk in ex.map(one, list(zip(starts, children[:-1]))[i:i + workers]):
+                fill_block(f0, blk)
+    return y
+
+
 def lognormal_node_sizes(rng: np.random.Generator, m: int, n: int,
                          mu: float = 5.0, sigma: float = 2.0) -> np.ndarray:
     """m node sizes ~ lognormal(mu, sigma) rescaled to sum to n (each >= 1)."""

@@ -116,3 +116,17 @@ def test_random_projections_recipe():
     assert set(np.unique(pr.sign)) == {-1, 1} and abs(pr.sign.mean()) < 0.02
     narrow = G.random_projections(np.random.default_rng(1), 500, 2, 3.0, 8)
     assert np.diff(narrow.ptr).max() == 2  # never more non-zeros than features
+
+
+def test_trunk_streamed_equals_trunk():
+    """The block-streamed Trunk generator hands over exactly trunk()'s values."""
+    n, p = 5000, 150
+    ref = G.trunk(n=n, p=p)
+    X = np.full((p, n), np.nan, dtype=np.float32)
+
+    def fill(f0, blk):
+        X[f0:f0 + blk.shape[0]] = blk
+
+    y = G.trunk_streamed(n, p, fill, workers=3)
+    np.testing.assert_array_equal(y, ref.y)
+    np.testing.assert_array_equal(X.view(np.uint32), ref.X.view(np.uint32))
