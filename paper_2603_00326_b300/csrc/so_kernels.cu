@@ -289,34 +289,48 @@ __global__ void __launch_bounds__(PG * 32) k_hist(DatasetView ds, const int32_t*
 // ============================================================================
 // K4a: Gini scan over the bins of every (histogram node, projection)
 // ============================================================================
-// One warp per (node, projection).  Lane l owns bins [l*BPL, l*BPL + BPL).
-struct BinPrefix {
-  int excl[kMaxClasses];  // counts of the bins before this lane's first bin
-  int N[kMaxClasses];     // node class counts
+// One warp per (node, projection).  The warp walks the bins in rounds of 32
+// consecutive bins, lane l taking bin 32 r + l, so that each load of a round
+// reads one contiguous run of counters; a warp scan per class and round
+// gives the left counts (bins <= b) of candidate b.
+struct BinWalk {
+  int N[kMaxClasses];      // node class counts
   long long n;
+  int carry[kMaxClasses];  // left counts before the current round
 };
 
-__device__ __forceinline__ void bin_prefix(const int32_t* __restrict__ H, int B, int C, int lane, int BPL,
-                                           BinPrefix& bp) {
-  int run[kMaxClasses];
-#pragma unroll
-  for (int c = 0; c < kMaxClasses; ++c) run[c] = 0;
-  for (int bb = 0; bb < BPL; ++bb) {
-    const int b = lane * BPL + bb;
-    if (b < B) {
-#pragma unroll
-      for (int c = 0; c < kMaxClasses; ++c)
-        if (c < C) run[c] += H[b * C + c];
-    }
-  }
-  bp.n = 0;
+__device__ __forceinline__ void walk_init(const int32_t* __restrict__ H, int B, int C, int lane, BinWalk& w) {
+  w.n = 0;
 #pragma unroll
   for (int c = 0; c < kMaxClasses; ++c) {
-    const int inc = warp_incl_scan(run[c], lane);
-    bp.excl[c] = inc - run[c];
-    bp.N[c] = __shfl_sync(0xffffffffu, inc, 31);
-    if (c < C) bp.n += bp.N[c];
+    w.N[c] = 0;
+    w.carry[c] = 0;
+    if (c < C) {
+      int t = 0;
+      for (int b = lane; b < B; b += 32) t += H[b * C + c];
+      w.N[c] = warp_sum(t);
+      w.n += w.N[c];
+    }
   }
+}
+
+// Left class counts L and left size of candidate b = 32 r + lane of round r
+// (rounds in order; every lane of the warp calls it).
+__device__ __forceinline__ long long walk_round(const int32_t* __restrict__ H, int B, int C, int lane, int r,
+                                                BinWalk& w, int* L) {
+  const int b = 32 * r + lane;
+  long long nL = 0;
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) {
+    L[c] = 0;
+    if (c < C) {
+      const int inc = warp_incl_scan(b < B ? H[b * C + c] : 0, lane);
+      L[c] = w.carry[c] + inc;
+      w.carry[c] += __shfl_sync(0xffffffffu, inc, 31);
+      nL += L[c];
+    }
+  }
+  return nL;
 }
 
 __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t P, int32_t B, int32_t C,
@@ -326,30 +340,21 @@ __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = plan_total->x * P;
-  const int BPL = (B + 31) / 32;
+  const int R = (B + 31) / 32;
   for (int64_t wi = gw; wi < total; wi += nw) {
     const int64_t h = wi / P;
     const int p = (int)(wi - h * P);
     const int32_t* H = hist + wi * (int64_t)B * C;
-    BinPrefix bp;
-    bin_prefix(H, B, C, lane, BPL, bp);
-    int L[kMaxClasses];
-#pragma unroll
-    for (int c = 0; c < kMaxClasses; ++c) L[c] = bp.excl[c];
+    BinWalk w;
+    walk_init(H, B, C, lane, w);
     float best = key_none(cr);
-    for (int bb = 0; bb < BPL; ++bb) {
-      const int b = lane * BPL + bb;
-      if (b > B - 2) break;
-      long long nL = 0;
-#pragma unroll
-      for (int c = 0; c < kMaxClasses; ++c) {
-        if (c < C) {
-          L[c] += H[b * C + c];
-          nL += L[c];
-        }
-      }
+    for (int r = 0; r < R; ++r) {
+      int L[kMaxClasses];
+      const long long nL = walk_round(H, B, C, lane, r, w, L);
+      const int b = 32 * r + lane;
+      if (b > B - 2) continue;
       float g = key_none(cr);
-      if (nL > 0 && nL < bp.n) g = key32(cr, L, bp.N, C, bp.n, nL);
+      if (nL > 0 && nL < w.n) g = key32(cr, L, w.N, C, w.n, nL);
       best = fmaxf(best, g);
       if (gain32_out) gain32_out[wi * (B - 1) + b] = g;
     }
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t
     if (p == 0) {
 #pragma unroll
       for (int c = 0; c < kMaxClasses; ++c)
-        if (c < C && lane == c) node_counts[h * C + c] = bp.N[c];
+        if (c < C && lane == c) node_counts[h * C + c] = w.N[c];
     }
   }
 }
@@ -377,7 +382,6 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
   __shared__ Cand s_best[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t m_hist = plan_total->x;
-  const int BPL = (B + 31) / 32;
   for (int64_t h = blockIdx.x; h < m_hist; h += gridDim.x) {
     const int j = hist_nodes[h];
     const int64_t n = off[j + 1] - off[j];
@@ -405,34 +409,24 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
     for (int p = warp; p < P; p += 8) {
       if (max32[h * P + p] < thr) continue;
       const int32_t* H = hist + (h * P + p) * (int64_t)B * C;
-      BinPrefix bp;
-      bin_prefix(H, B, C, lane, BPL, bp);
-      int L[kMaxClasses];
-      long long prev_nL = 0;  // left size of the candidate before this lane's first
-#pragma unroll
-      for (int c = 0; c < kMaxClasses; ++c) {
-        L[c] = bp.excl[c];
-        if (c < C) prev_nL += L[c];
-      }
-      for (int bb = 0; bb < BPL; ++bb) {
-        const int b = lane * BPL + bb;
-        if (b > B - 2) break;
-        long long nL = 0;
-#pragma unroll
-        for (int c = 0; c < kMaxClasses; ++c) {
-          if (c < C) {
-            L[c] += H[b * C + c];
-            nL += L[c];
-          }
-        }
+      BinWalk w;
+      walk_init(H, B, C, lane, w);
+      long long before = 0;  // left size of bin 32 r - 1
+      for (int r = 0; r * 32 < B; ++r) {
+        int L[kMaxClasses];
+        const long long nL = walk_round(H, B, C, lane, r, w, L);
+        long long prev = __shfl_up_sync(0xffffffffu, nL, 1);
+        if (lane == 0) prev = before;
+        before = __shfl_sync(0xffffffffu, nL, 31);
+        const int b = 32 * r + lane;
+        if (b > B - 2) continue;
         // an empty bin b repeats candidate b-1's partition (same double gain
         // bits, lower index), so it can never be the lexicographic argmax
-        const bool repeat = b > 0 && nL == prev_nL;
-        prev_nL = nL;
-        if (!repeat && nL > 0 && nL < bp.n) {
-          const float g = key32(cr, L, bp.N, C, bp.n, nL);
+        const bool repeat = b > 0 && nL == prev;
+        if (!repeat && nL > 0 && nL < w.n) {
+          const float g = key32(cr, L, w.N, C, w.n, nL);
           if (g >= thr) {
-            const Cand c{gain64c(cr, L, bp.N, C, bp.n, nL), p, b};
+            const Cand c{gain64c(cr, L, w.N, C, w.n, nL), p, b};
             if (better(c, best)) best = c;
           }
         }
