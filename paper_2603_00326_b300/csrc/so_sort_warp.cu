@@ -91,8 +91,10 @@ struct SortNodeCtx {
 };
 
 // Loads, projects and sorts one projection of one node; returns the lane's
-// keys in k[] (padding keys are all-ones and sort last).
-template <int EPL>
+// keys in k[] (padding keys are all-ones and sort last).  RM: gather from the
+// row-major copy ds.Xr (the node's projections then share its samples' rows
+// through L2) instead of one sector per (sample, feature) of the columns.
+template <int EPL, int RM>
 __device__ __forceinline__ void load_sort(const DatasetView& ds, const int32_t* __restrict__ idx, const ProjView& pv,
                                           int64_t q, const SortNodeCtx& nc, int lane, unsigned long long (&k)[EPL]) {
   const int rb = pv.beg[q];
@@ -122,9 +124,10 @@ __device__ __forceinline__ void load_sort(const DatasetView& ds, const int32_t* 
       const int jj = j0 + u < kk ? j0 + u : j0;
       const int f = __shfl_sync(0xffffffffu, fl, jj);
       sg[u] = __shfl_sync(0xffffffffu, sl, jj);
-      const float* col = ds.X + (int64_t)f * ds.ld;
+      const float* col = RM ? ds.Xr + f : ds.X + (int64_t)f * ds.ld;
 #pragma unroll
-      for (int r = 0; r < EPL; ++r) x[u][r] = (j0 + u < kk && sid[r] >= 0) ? __ldg(col + sid[r]) : 0.0f;
+      for (int r = 0; r < EPL; ++r)
+        x[u][r] = (j0 + u < kk && sid[r] >= 0) ? __ldg(col + (RM ? (int64_t)sid[r] * ds.d : (int64_t)sid[r])) : 0.0f;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -279,12 +282,12 @@ __device__ __forceinline__ void score_projection(const SortNodeCtx& nc, int C, c
   }
 }
 
-template <int EPL>
+template <int EPL, int RM>
 __device__ __forceinline__ void proj_pass1_reg(const DatasetView& ds, const int32_t* idx, const ProjView& pv, int64_t q,
                                                const SortNodeCtx& nc, int lane, const Crit& cr, bool rescore,
                                                SortRes* out) {
   unsigned long long k[EPL];
-  load_sort<EPL>(ds, idx, pv, q, nc, lane, k);
+  load_sort<EPL, RM>(ds, idx, pv, q, nc, lane, k);
   score_projection(nc, ds.C, cr, lane, [&](auto visit) { scan_candidates<EPL>(k, nc, ds.C, cr, lane, visit); },
                    rescore, out);
 }
@@ -300,7 +303,7 @@ __device__ __forceinline__ int epl_of(int nv) { return nv <= 32 ? 1 : nv <= 64 ?
 // the double re-score, only the projections whose maximum reaches their
 // node's window (listed by k_sort_node_thr) -- the only ones the selection
 // reads.
-template <int ENT>
+template <int ENT, int RM>
 __global__ void __launch_bounds__(256, 4) k_sortw_scan(DatasetView ds, const int32_t* __restrict__ idx,
                                                        const int64_t* __restrict__ off, ProjView pv,
                                                        const V4* plan_total, const int32_t* nodes,
@@ -331,9 +334,9 @@ __global__ void __launch_bounds__(256, 4) k_sortw_scan(DatasetView ds, const int
     const int64_t q = (int64_t)j * P + p;
     SortRes* out = res + q;
     switch (epl_of(nc.nv)) {
-      case 1: proj_pass1_reg<1>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
-      case 2: proj_pass1_reg<2>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
-      default: proj_pass1_reg<4>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
+      case 1: proj_pass1_reg<1, RM>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
+      case 2: proj_pass1_reg<2, RM>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
+      default: proj_pass1_reg<4, RM>(ds, idx, pv, q, nc, lane, cr, rescore, out); break;
     }
   }
 }
@@ -755,7 +758,8 @@ cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan
   int NPmax = 2 * kScThreads;
   while (NPmax < a.T - 1) NPmax <<= 1;
   const size_t smem = (size_t)NPmax * 8;
-  auto kw = cr.ent ? k_sortw_scan<1> : k_sortw_scan<0>;
+  auto kw = cr.ent ? (a.ds.Xr ? k_sortw_scan<1, 1> : k_sortw_scan<1, 0>)
+                   : (a.ds.Xr ? k_sortw_scan<0, 1> : k_sortw_scan<0, 0>);
   auto kc = cr.ent ? (a.ds.Xr ? k_sortc_scan<1, 1> : k_sortc_scan<1, 0>)
                    : (a.ds.Xr ? k_sortc_scan<0, 1> : k_sortc_scan<0, 0>);
   // every projection's float maximum; then each node's window; then the
