@@ -4,8 +4,9 @@
 // Pass 1, per (node, projection): gather the node's projected values and sort
 // the (order-preserving key, label) pairs -- one warp in registers for nodes
 // of up to kSortRegMax samples (bitonic network, lane-major layout
-// e = lane*EPL + r), one CTA in shared memory for larger exact-path nodes --
-// form class prefix counts with a packed scan, evaluate the float key of the
+// e = lane*EPL + r), one CTA in shared memory for larger exact-path nodes
+// (a bitonic network up to kScBitonicMax samples, a segmented radix sort of
+// the value keys above) -- form class prefix counts with a packed scan, evaluate the float key of the
 // criterion at every boundary between distinct values and keep the
 // projection's float maximum M_p.  k_sort_node_thr then sets each node's
 // window below M = max_p M_p, and a second pass redoes only the projections
@@ -344,11 +345,17 @@ __global__ void __launch_bounds__(256, 4) k_sortw_scan(DatasetView ds, const int
 // Pass 1, CTA form: one CTA of kScThreads per (node of kSortRegMax+1 .. T-1
 // samples, projection).  The node's projected values are gathered by the
 // whole CTA (each thread up to NP/kScThreads samples, the projection's terms
-// four at a time), sorted as (key, label) pairs with a shared-memory bitonic
-// network, and scanned in per-thread chunks of consecutive sorted positions
-// with a block-wide exclusive scan of the packed class counters.
+// four at a time), sorted in shared memory (nodes of up to kScBitonicMax
+// samples as (key, label) pairs by a bitonic network, larger ones by value
+// key with a segmented radix sort, sc_radix), and scanned in per-thread
+// chunks of consecutive sorted positions with a block-wide exclusive scan of
+// the packed class counters.
 constexpr int kScThreads = 128;
 constexpr int kScWarps = kScThreads / 32;
+// CTA-sorted nodes of up to this many samples take the bitonic network, larger
+// ones the radix passes (measured: the network is faster for 129..256
+// samples, the radix passes from about 500 up)
+constexpr int kScBitonicMax = 256;
 
 struct ScShared {
   int feat[kMaxCap];
@@ -356,6 +363,8 @@ struct ScShared {
   unsigned long long wlo[kScWarps], whi[kScWarps];
   float wmax[kScWarps];
   Best wbest[kScWarps];
+  unsigned kor[kScWarps], kand[kScWarps];  // radix: bits set in some / every key of the node
+  int wtot[kScWarps];                      // radix: warp totals of the digit-count scan
 };
 
 // Shared-memory slot of sorted position p: bits 0-3 are XORed with bits 4-7,
@@ -370,9 +379,10 @@ __device__ __forceinline__ int sc_slot(int p) { return p ^ ((p >> 4) & 15); }
 // RM: read the row-major copy ds.Xr (the node's projections then share its
 // samples' rows through L2) instead of one sector per (sample, feature) of
 // the columns.
-template <int RM>
+// The thread's OR and AND of its keys' value bits go to kor / kand.
+template <int RM, class Put>
 __device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* __restrict__ idx, const SortNodeCtx& nc,
-                                          int kk, const ScShared& sh, unsigned long long* keys) {
+                                          int kk, const ScShared& sh, Put put, unsigned& kor, unsigned& kand) {
   constexpr int kPer = 4;  // samples per thread per round, loads of 4 terms in flight per sample
   for (int e0 = threadIdx.x; e0 < nc.nv; e0 += kScThreads * kPer) {
     int64_t sid[kPer];
@@ -405,7 +415,12 @@ __device__ __forceinline__ void sc_gather(const DatasetView& ds, const int32_t* 
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = e0 + u * kScThreads;
-      if (sid[u] >= 0) keys[sc_slot(e)] = ((unsigned long long)f2key(v[u]) << 32) | (unsigned long long)(unsigned)ds.y[sid[u]];
+      if (sid[u] >= 0) {
+        const unsigned kv = f2key(v[u]);
+        kor |= kv;
+        kand &= kv;
+        put(e, kv, (unsigned)ds.y[sid[u]]);
+      }
     }
   }
 }
@@ -481,17 +496,108 @@ __device__ __forceinline__ void sc_bitonic(unsigned long long* keys, int NP, int
   }
 }
 
+// Segmented radix sort of one node's pairs by the 32-bit value key (least
+// significant digit first, 8-bit digits; a digit that is the same in every key
+// of the node, bits diff = OR ^ AND of the keys, is skipped).  Value keys and
+// labels sit in separate arrays with two buffers each (buffer b at offset
+// b * np_max, position i at slot sc_slot(i)); each pass moves positions
+// 0..nv-1 stably to the other buffer.  Warp w owns the segment
+// [w * seg, (w + 1) * seg) of positions: it counts its digits with
+// shared-memory reductions; the digit-major, warp-minor exclusive scan of the
+// counts gives every (digit, warp) its first output position; the warp then
+// walks its segment in order, 32 positions at a time, lanes holding the same
+// digit finding each other with a match and their leader taking the group's
+// positions from the running offset.  Counts and offsets are 16-bit halves of
+// [kScWarps][128] words (digit dg: word dg >> 1, half dg & 1; both stay below
+// 2048); cnt holds two such arrays, a pass counting in cnt[par] (zero on
+// entry) and clearing cnt[par ^ 1] for the next.  Returns the buffer holding
+// the sorted pairs.
+__device__ __forceinline__ int sc_radix(unsigned* k32, uint8_t* l8, int np_max, int nv, unsigned diff,
+                                             unsigned* cnt, int& par, ScShared& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = ((((nv + kScWarps - 1) / kScWarps) + 31) >> 5) << 5;
+  const int p0 = warp * seg, p1 = min(nv, p0 + seg);
+  const unsigned lt = (1u << lane) - 1u;
+  int cur = 0;
+  for (int sh8 = 0; sh8 < 32; sh8 += 8) {
+    if (((diff >> sh8) & 255u) == 0u) continue;
+    unsigned* c = cnt + par * (kScWarps * 128);
+    unsigned* cn = cnt + (par ^ 1) * (kScWarps * 128);
+    unsigned* wc = c + warp * 128;
+    const unsigned* ka = k32 + cur * np_max;
+    const uint8_t* la = l8 + cur * np_max;
+    unsigned* kb = k32 + (cur ^ 1) * np_max;
+    uint8_t* lb = l8 + (cur ^ 1) * np_max;
+    for (int p = p0 + lane; p < p1; p += 32) {
+      const unsigned dg = (ka[sc_slot(p)] >> sh8) & 255u;
+      atomicAdd(&wc[dg >> 1], 1u << (16 * (dg & 1u)));
+    }
+    __syncthreads();
+    // exclusive scan in (digit, warp) order: thread t takes digits 2t, 2t+1 (word t)
+    unsigned v[kScWarps];
+    int tot = 0;
+#pragma unroll
+    for (int w = 0; w < kScWarps; ++w) {
+      v[w] = c[w * 128 + threadIdx.x];
+      tot += (int)(v[w] & 0xFFFFu) + (int)(v[w] >> 16);
+    }
+    const int inc = warp_incl_scan(tot, lane);
+    if (lane == 31) sh.wtot[warp] = inc;
+    __syncthreads();
+    int run = inc - tot;
+    for (int w = 0; w < warp; ++w) run += sh.wtot[w];
+    unsigned o[kScWarps];
+#pragma unroll
+    for (int w = 0; w < kScWarps; ++w) {
+      o[w] = (unsigned)run;
+      run += (int)(v[w] & 0xFFFFu);
+    }
+#pragma unroll
+    for (int w = 0; w < kScWarps; ++w) {
+      o[w] |= (unsigned)run << 16;
+      run += (int)(v[w] >> 16);
+    }
+#pragma unroll
+    for (int w = 0; w < kScWarps; ++w) c[w * 128 + threadIdx.x] = o[w];
+    __syncthreads();
+    for (int pb = p0; pb < p1; pb += 32) {
+      const int p = pb + lane;
+      const bool valid = p < p1;
+      const int sp = sc_slot(valid ? p : p0);
+      const unsigned kv = ka[sp];
+      const unsigned dg = valid ? (kv >> sh8) & 255u : 256u + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      const int leader = __ffs(peers) - 1;
+      const unsigned hs = 16u * (dg & 1u);
+      unsigned pos = 0u;
+      if (valid && lane == leader) pos = (atomicAdd(&wc[dg >> 1], (unsigned)__popc(peers) << hs) >> hs) & 0xFFFFu;
+      pos = __shfl_sync(0xffffffffu, pos, leader);
+      if (valid) {
+        const int dp = sc_slot((int)pos + __popc(peers & lt));
+        kb[dp] = kv;
+        lb[dp] = la[sp];
+      }
+      __syncwarp();
+    }
+    for (int i = threadIdx.x; i < kScWarps * 128; i += kScThreads) cn[i] = 0u;
+    __syncthreads();
+    cur ^= 1;
+    par ^= 1;
+  }
+  return cur;
+}
+
 // Walks this thread's chunk [i0, i0+E) of sorted positions; calls
 // visit(i, run, g32, a, b) for each candidate (boundary between distinct
 // values), run = packed class counts of positions 0..i.
-template <class Visit>
-__device__ __forceinline__ void sc_walk(const unsigned long long* keys, const SortNodeCtx& nc, int C, const Crit& cr,
+template <class Get, class Visit>
+__device__ __forceinline__ void sc_walk(Get key_at, const SortNodeCtx& nc, int C, const Crit& cr,
                                         int i0, int E, PackedCnt run, Visit visit) {
-  unsigned long long x = i0 < nc.nv - 1 ? keys[sc_slot(i0)] : 0ull;
+  unsigned long long x = i0 < nc.nv - 1 ? key_at(i0) : 0ull;
   for (int e = 0; e < E; ++e) {
     const int i = i0 + e;
     if (i >= nc.nv - 1) break;
-    const unsigned long long nx = keys[sc_slot(i + 1)];
+    const unsigned long long nx = key_at(i + 1);
     pc_add(run, (int)(x & 0xFFull));
     const unsigned a = (unsigned)(x >> 32), b = (unsigned)(nx >> 32);
     x = nx;
@@ -512,12 +618,17 @@ __global__ void __launch_bounds__(kScThreads, 8) k_sortc_scan(DatasetView ds, co
                                                              const int64_t* __restrict__ off, ProjView pv,
                                                              const V4* plan_total, const int32_t* nodes,
                                                              const int32_t* __restrict__ node_cls, Crit cr_in,
-                                                             SortRes* res) {
+                                                             SortRes* res, int np_max) {
   Crit cr = cr_in;
   cr.ent = ENT;
-  extern __shared__ unsigned long long s_keys[];  // [NP <= kMaxSortBelow]
+  // bitonic: pairs [NP]; radix: value keys [2][np_max], then labels [2][np_max]
+  extern __shared__ unsigned long long s_keys[];
   __shared__ ScShared sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // radix digit counts: two arrays of [kScWarps][128] words
+  __shared__ unsigned s_rcnt[2 * kScWarps * 128];
+  int rpar = 0;
+  for (int i = threadIdx.x; i < kScWarps * 128; i += kScThreads) s_rcnt[i] = 0u;
   const int P = pv.P;
   const int64_t total = plan_total->w * P;
   for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
@@ -539,15 +650,51 @@ __global__ void __launch_bounds__(kScThreads, 8) k_sortc_scan(DatasetView ds, co
       sh.sign[threadIdx.x] = pv.sign[rb + threadIdx.x];
     }
     __syncthreads();
-    sc_gather<RM>(ds, idx, nc, kk, sh, s_keys);
-    __syncthreads();
-    sc_bitonic(s_keys, NP, nc.nv);
+    // nodes of up to kScBitonicMax samples: (key, label) pairs sorted by the
+    // bitonic network; larger nodes: value keys and labels in separate
+    // arrays, sorted by the radix passes
+    const bool rdx = nc.nv > kScBitonicMax;
+    unsigned* s_k32 = reinterpret_cast<unsigned*>(s_keys);             // [2][np_max] value keys
+    uint8_t* s_l8 = reinterpret_cast<uint8_t*>(s_k32 + 2 * np_max);  // [2][np_max] labels
+    unsigned kor = 0u, kand = ~0u;
+    sc_gather<RM>(ds, idx, nc, kk, sh, [&](int e, unsigned kv, unsigned yv) {
+      if (rdx) {
+        s_k32[sc_slot(e)] = kv;
+        s_l8[sc_slot(e)] = (uint8_t)yv;
+      } else {
+        s_keys[sc_slot(e)] = ((unsigned long long)kv << 32) | (unsigned long long)yv;
+      }
+    }, kor, kand);
+    int fin = 0;
+    if (rdx) {
+      kor = __reduce_or_sync(0xffffffffu, kor);
+      kand = __reduce_and_sync(0xffffffffu, kand);
+      if (lane == 0) {
+        sh.kor[warp] = kor;
+        sh.kand[warp] = kand;
+      }
+      __syncthreads();
+      for (int w = 0; w < kScWarps; ++w) {
+        kor |= sh.kor[w];
+        kand &= sh.kand[w];
+      }
+      fin = sc_radix(s_k32, s_l8, np_max, nc.nv, kor ^ kand, s_rcnt, rpar, sh);
+    } else {
+      __syncthreads();
+      sc_bitonic(s_keys, NP, nc.nv);
+    }
+    const unsigned* kf = s_k32 + fin * np_max;
+    const uint8_t* lf = s_l8 + fin * np_max;
+    auto key_at = [&](int i) -> unsigned long long {
+      const int sl = sc_slot(i);
+      return rdx ? ((unsigned long long)kf[sl] << 32) | (unsigned long long)lf[sl] : s_keys[sl];
+    };
     // this thread's chunk of consecutive sorted positions and its left counts
     const int E = NP / kScThreads;
     const int i0 = threadIdx.x * E;
     PackedCnt own{0, 0};
     for (int e = 0; e < E; ++e)
-      if (i0 + e < nc.nv) pc_add(own, (int)(s_keys[sc_slot(i0 + e)] & 0xFFull));
+      if (i0 + e < nc.nv) pc_add(own, (int)(key_at(i0 + e) & 0xFFull));
     unsigned long long ilo = own.lo, ihi = own.hi;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -570,7 +717,7 @@ __global__ void __launch_bounds__(kScThreads, 8) k_sortc_scan(DatasetView ds, co
     }
     // float maximum of the projection
     float m = key_none(cr);
-    sc_walk(s_keys, nc, ds.C, cr, i0, E, run,
+    sc_walk(key_at, nc, ds.C, cr, i0, E, run,
             [&](int, const PackedCnt&, float g, unsigned, unsigned) { m = fmaxf(m, g); });
     m = warp_max(m);
     if (lane == 0) sh.wmax[warp] = m;
@@ -584,7 +731,7 @@ __global__ void __launch_bounds__(kScThreads, 8) k_sortc_scan(DatasetView ds, co
     lb.L = PackedCnt{0, 0};
     if (key_any(cr, m)) {
       const float thr = key_thr(cr, m, nc.nv, ds.C);
-      sc_walk(s_keys, nc, ds.C, cr, i0, E, run, [&](int i, const PackedCnt& r, float g, unsigned a, unsigned b) {
+      sc_walk(key_at, nc, ds.C, cr, i0, E, run, [&](int i, const PackedCnt& r, float g, unsigned a, unsigned b) {
         if (g >= thr) {
           int L[kMaxClasses];
 #pragma unroll
@@ -757,7 +904,9 @@ cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan
   const bool cta = !a.hist_only && a.T > kSortRegMax + 1;
   int NPmax = 2 * kScThreads;
   while (NPmax < a.T - 1) NPmax <<= 1;
-  const size_t smem = (size_t)NPmax * 8;
+  // the larger of the bitonic network's pairs (8 bytes a position) and the
+  // radix passes' two buffers of value keys and labels (10 bytes a position)
+  const size_t smem = (size_t)NPmax * (NPmax > kScBitonicMax ? 10 : 8);
   auto kw = cr.ent ? (a.ds.Xr ? k_sortw_scan<1, 1> : k_sortw_scan<1, 0>)
                    : (a.ds.Xr ? k_sortw_scan<0, 1> : k_sortw_scan<0, 0>);
   auto kc = cr.ent ? (a.ds.Xr ? k_sortc_scan<1, 1> : k_sortc_scan<1, 0>)
@@ -774,7 +923,7 @@ cudaError_t launch_sort_warp(const SearchArgs& a, const Crit& cr, const V4* plan
     if (cta && pass == 0) {  // CTA-sorted nodes: one pass, re-score inline
       ProfScope ps_("k_sortc_scan", st);
       kc<<<di.num_sms * 16, kScThreads, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, plan_total, med, node_cls, cr,
-                                                    res);
+                                                    res, NPmax);
     }
     if (pass == 0) {
       ProfScope ps_("k_sort_node_thr", st);
