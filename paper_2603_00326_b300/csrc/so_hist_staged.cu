@@ -193,14 +193,22 @@ struct ItemPos {
   int p0, np;
 };
 
+// The item's node h = the last node whose first item is <= t, by a 32-way
+// search: each step the warp probes 32 evenly spaced first-item offsets at
+// once (item_off is nondecreasing, so the probes at or below t form a prefix
+// of the lanes), cutting the range 32-fold per dependent load.
 __device__ __forceinline__ ItemPos decode_item(const StagedPlan& sp, int64_t t, int P) {
   ItemPos r;
   const int64_t m_hist = sp.plan_total->x;
-  int64_t lo = 0, hi = m_hist - 1;
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = m_hist - 1;  // item_off[lo] <= t; h in [lo, hi]
   while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (sp.item_off[mid] <= t) lo = mid;
-    else hi = mid - 1;
+    const int64_t step = (hi - lo + 31) >> 5;
+    const int64_t pos = lo + (int64_t)(lane + 1) * step;
+    const bool ok = pos <= hi && sp.item_off[pos] <= t;
+    const int c = __popc(__ballot_sync(0xffffffffu, ok));
+    hi = min(hi, lo + (int64_t)(c + 1) * step - 1);
+    lo += (int64_t)c * step;
   }
   r.h = lo;
   r.j = sp.hist_nodes[lo];
