@@ -210,7 +210,7 @@ def gain_error(S, torch, ds, ds_np, pr, idx, off, n_proj=8):
 
 
 def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=True, batched_only=False,
-               wide_n=None):
+               wide_n=None, frontier_fixed=None):
     """Secondary measurements: the batched frontier against the node-at-a-time
     form on the same GPU (frontier_1m: n=1M, d=128, 4096 lognormal nodes,
     64 projections/node, crossover T autotuned), one tree grown to purity
@@ -241,7 +241,14 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=T
     off = torch.from_numpy(off_np).to(dev)
     # the crossover T from the start-up microbenchmark (Section 3.1), as this
     # workload specifies; both forms below use it
-    prm, tune_sizes, tune_ms = S.so_autotune(dd, P, p["lam"], int(p["cap"]), S.split_params(256, p["sort_below"], False))
+    if frontier_fixed:
+        # profiling case: the given crossover and decomposition instead of the
+        # start-up microbenchmark (whose timings a profiler distorts)
+        T_, ppc_, ch_ = frontier_fixed
+        prm = S.split_params(256, T_, False, proj_per_cta=ppc_, chunk=ch_)
+    else:
+        prm, tune_sizes, tune_ms = S.so_autotune(dd, P, p["lam"], int(p["cap"]),
+                                                 S.split_params(256, p["sort_below"], False))
     ws = torch.empty(S.so_split_search_ws_bytes(m, ds_np.n, P, 2, prm), dtype=torch.uint8, device=dev)
     outb = torch.empty(m * S.SPLIT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     for _ in range(3):
@@ -255,7 +262,9 @@ def extra_legs(S, torch, dev, forest_trees=2, only=None, wide_trees=1, rw_tree=T
     batched_ms = (time.perf_counter() - t0) * 1000.0 / reps
     sp = float(ds_np.n * P)
     if batched_only:
-        return {"frontier_1m": {"nodes": m, "autotuned_sort_below": int(prm.sort_below), "batched_ms": batched_ms,
+        return {"frontier_1m": {"nodes": m, ("fixed_sort_below" if frontier_fixed else "autotuned_sort_below"):
+                                int(prm.sort_below), "proj_per_cta": int(prm.proj_per_cta), "chunk": int(prm.chunk),
+                                "batched_ms": batched_ms,
                                 "batched_sample_projections_per_s": sp / (batched_ms / 1000.0)}}
     # node-at-a-time: one synchronous call per node (the paper's offload form)
     views = []
@@ -510,7 +519,8 @@ def run_leg(args):
     # trees run in the default extras and in --leg rw)
     out = extra_legs(S, torch, dev, args.forest_trees if args.leg == "forest" else 0, only=args.leg,
                      wide_trees=args.wide_trees if args.leg == "wide" else 0, rw_tree=False,
-                     batched_only=args.batched_only, wide_n=args.wide_n)
+                     batched_only=args.batched_only, wide_n=args.wide_n,
+                     frontier_fixed=tuple(int(v) for v in args.frontier_fixed.split(",")) if args.frontier_fixed else None)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
     return 0
 
@@ -784,6 +794,9 @@ def main():
                     help="profiling case: the wide tree on this many samples (same recipe)")
     ap.add_argument("--batched-only", action="store_true",
                     help="frontier leg: time the batched search only (no node-at-a-time loop)")
+    ap.add_argument("--frontier-fixed", default=None, metavar="T,PPC,CHUNK",
+                    help="profiling case: frontier leg with this crossover, projections per CTA and chunk "
+                         "instead of the autotuner's")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
