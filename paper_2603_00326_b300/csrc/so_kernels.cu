@@ -435,44 +435,59 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
     best = warp_best(best);
     if (lane == 0) s_best[warp] = best;
     __syncthreads();
-    if (threadIdx.x == 0 && !(s_best[0].g > 0.0 || s_best[1].g > 0.0 || s_best[2].g > 0.0 || s_best[3].g > 0.0 ||
-                              s_best[4].g > 0.0 || s_best[5].g > 0.0 || s_best[6].g > 0.0 || s_best[7].g > 0.0)) {
-      // no re-scored candidate with a positive double gain (information gain
-      // can round to zero or below for a split that carries almost none)
-      so_split r;
-      r.valid = 0; r.proj = -1; r.path = 0; r.cand = -1; r.threshold = 0.0f; r.gain = 0.0;
-      r.n_left = 0; r.n_right = 0;
-      out[j] = r;
-      if (left_counts)
-        for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = 0;
-    } else if (threadIdx.x == 0) {
+    if (warp == 0) {
+      // every lane of warp 0 takes the node's best; the left class counts of
+      // the chosen candidate are summed over its bins 32 at a time
       Cand f = s_best[0];
       for (int w = 1; w < 8; ++w)
         if (better(s_best[w], f)) f = s_best[w];
-      if (f.proj == INT_MAX) f.proj = 0, f.cand = 0;  // cannot happen: the float maximum is always re-scored
-      const int32_t* H = hist + (h * P + f.proj) * (int64_t)B * C;
-      long long Lc[kMaxClasses];
-      long long nL = 0;
-      for (int c = 0; c < C; ++c) Lc[c] = 0;
-      for (int b = 0; b <= f.cand; ++b)
-        for (int c = 0; c < C; ++c) Lc[c] += H[b * C + c];
-      for (int c = 0; c < C; ++c) nL += Lc[c];
-      const float mn = key2f(mm[(h * P + f.proj) * 2]);
-      const float mx = key2f(mm[(h * P + f.proj) * 2 + 1]);
-      const float w = bin_width(mn, mx, B);
-      so_split r;
-      r.valid = 1;
-      r.proj = f.proj;
-      r.path = 0;
-      r.cand = f.cand;
-      // candidate b's threshold is boundary t_{b+1}
-      r.threshold = rw_t ? rw_t[(h * P + f.proj) * kRwRow + f.cand] : boundary(mn, w, f.cand + 1);
-      r.gain = f.g;
-      r.n_left = nL;
-      r.n_right = n - nL;
-      out[j] = r;
-      if (left_counts)
-        for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = Lc[c];
+      if (!(f.g > 0.0)) {
+        // no re-scored candidate with a positive double gain (information
+        // gain can round to zero or below for a split that carries almost none)
+        if (lane == 0) {
+          so_split r;
+          r.valid = 0; r.proj = -1; r.path = 0; r.cand = -1; r.threshold = 0.0f; r.gain = 0.0;
+          r.n_left = 0; r.n_right = 0;
+          out[j] = r;
+          if (left_counts)
+            for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = 0;
+        }
+      } else {
+        if (f.proj == INT_MAX) f.proj = 0, f.cand = 0;  // cannot happen: the float maximum is always re-scored
+        const int32_t* H = hist + (h * P + f.proj) * (int64_t)B * C;
+        long long Lc[kMaxClasses];
+#pragma unroll
+        for (int c = 0; c < kMaxClasses; ++c) Lc[c] = 0;
+        for (int b = lane; b <= f.cand; b += 32)
+#pragma unroll
+          for (int c = 0; c < kMaxClasses; ++c)
+            if (c < C) Lc[c] += H[b * C + c];
+        long long nL = 0;
+#pragma unroll
+        for (int c = 0; c < kMaxClasses; ++c) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) Lc[c] += __shfl_xor_sync(0xffffffffu, Lc[c], o);
+          nL += c < C ? Lc[c] : 0;
+        }
+        if (lane == 0) {
+          const float mn = key2f(mm[(h * P + f.proj) * 2]);
+          const float mx = key2f(mm[(h * P + f.proj) * 2 + 1]);
+          const float w = bin_width(mn, mx, B);
+          so_split r;
+          r.valid = 1;
+          r.proj = f.proj;
+          r.path = 0;
+          r.cand = f.cand;
+          // candidate b's threshold is boundary t_{b+1}
+          r.threshold = rw_t ? rw_t[(h * P + f.proj) * kRwRow + f.cand] : boundary(mn, w, f.cand + 1);
+          r.gain = f.g;
+          r.n_left = nL;
+          r.n_right = n - nL;
+          out[j] = r;
+          if (left_counts)
+            for (int c = 0; c < C; ++c) left_counts[(int64_t)j * C + c] = Lc[c];
+        }
+      }
     }
     __syncthreads();
   }
@@ -655,10 +670,13 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
     k_hist_select<<<grid_fill, 256, 0, st>>>(s.plan_total, s.hist_nodes, a.node_off, P, B, C, s.hist, s.max32,
                                              s.mm_keys, rw ? s.rw.t : nullptr, cr, a.out, a.left_counts);
   }
-  // exact path
-  e = launch_sort_warp(a, cr, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls,
-                       s.sort_lists, s.sort_list_n, st);
-  if (e != cudaSuccess) return e;
+  // exact path (no node can take it when every node is on the histogram path
+  // or T <= 2: nodes below 2 samples are never searched)
+  if (!a.hist_only && a.T > 2) {
+    e = launch_sort_warp(a, cr, s.plan_total, s.sort_nodes, s.sort_nodes + a.m + 1, s.sort_res, s.node_cls,
+                         s.sort_lists, s.sort_list_n, st);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
@@ -841,21 +859,68 @@ __device__ __forceinline__ int part_flag(const PartArgs& a, const PartNode& nd, 
 
 __global__ void __launch_bounds__(kPartThreads) k_part_flags(PartArgs a) {
   const int64_t base = (int64_t)blockIdx.x * kPartTile;
+  const int64_t q0 = base + threadIdx.x;  // the thread's samples: q0 + k * kPartThreads
   int cnt = 0;
-  int j = -1;
-  int64_t seg_end = -1;
-  PartNode nd;
-  for (int k = 0; k < kPartPer; ++k) {
-    const int64_t q = base + (int64_t)k * kPartThreads + threadIdx.x;
-    if (q >= a.n) break;
-    if (j < 0 || q >= seg_end) {
-      j = find_seg(a.node_off, a.m, q);
-      nd = a.nodes[j];
-      seg_end = a.node_off[j + 1];
+  int j = q0 < a.n ? find_seg(a.node_off, a.m, q0) : -1;
+  const int64_t q_last = min(a.n - 1, q0 + (int64_t)(kPartPer - 1) * kPartThreads);
+  if (j >= 0 && a.node_off[j + 1] > q_last) {
+    // every sample of the thread in one node: the sample ids first, then each
+    // term's values of all of them, so the loads of a stage are in flight
+    // together; the terms are added in row order as part_flag does
+    const PartNode nd = a.nodes[j];
+    int32_t sid[kPartPer];
+#pragma unroll
+    for (int k = 0; k < kPartPer; ++k) {
+      const int64_t q = q0 + (int64_t)k * kPartThreads;
+      sid[k] = q < a.n ? (int32_t)safe_sample(a.idx_in[q], a.ds.n) : 0;
     }
-    const int f = part_flag(a, nd, (int32_t)safe_sample(a.idx_in[q], a.ds.n));
-    a.flags[q] = (uint8_t)f;
-    cnt += f;
+    int fl[kPartPer];
+    if (nd.mode == PART_COPY || nd.mode == PART_DROP) {
+#pragma unroll
+      for (int k = 0; k < kPartPer; ++k) fl[k] = nd.mode == PART_COPY ? 1 : 0;
+    } else {
+      const int kk = nd.nnz < 0 ? 0 : (nd.nnz > kMaxCap ? kMaxCap : nd.nnz);
+      float acc[kPartPer];
+#pragma unroll
+      for (int k = 0; k < kPartPer; ++k) acc[k] = 0.0f;
+      for (int jj = 0; jj < kk; ++jj) {
+        int f = a.feat[nd.feat_off + jj];
+        f = (f < 0 || f >= a.ds.d) ? 0 : f;
+        const bool pos = a.sign[nd.feat_off + jj] == 1;
+        const float* col = a.ds.X + (int64_t)f * a.ds.ld;
+        float x[kPartPer];
+#pragma unroll
+        for (int k = 0; k < kPartPer; ++k) x[k] = __ldg(col + sid[k]);
+#pragma unroll
+        for (int k = 0; k < kPartPer; ++k) acc[k] = __fadd_rn(acc[k], pos ? x[k] : -x[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < kPartPer; ++k) fl[k] = acc[k] < nd.thr ? 1 : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kPartPer; ++k) {
+      const int64_t q = q0 + (int64_t)k * kPartThreads;
+      if (q < a.n) {
+        a.flags[q] = (uint8_t)fl[k];
+        cnt += fl[k];
+      }
+    }
+  } else if (j >= 0) {
+    int64_t seg_end = -1;
+    j = -1;
+    PartNode nd;
+    for (int k = 0; k < kPartPer; ++k) {
+      const int64_t q = q0 + (int64_t)k * kPartThreads;
+      if (q >= a.n) break;
+      if (j < 0 || q >= seg_end) {
+        j = find_seg(a.node_off, a.m, q);
+        nd = a.nodes[j];
+        seg_end = a.node_off[j + 1];
+      }
+      const int f = part_flag(a, nd, (int32_t)safe_sample(a.idx_in[q], a.ds.n));
+      a.flags[q] = (uint8_t)f;
+      cnt += f;
+    }
   }
   cnt = warp_sum(cnt);
   __shared__ int s_c[kPartThreads / 32];
@@ -907,12 +972,28 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(PartArgs a) {
   const int64_t q0 = tile0 + (int64_t)threadIdx.x * kPartPer;
   int cnt = 0;
   uint8_t fl[kPartPer];
+  int32_t iv[kPartPer];  // the samples' entries, loaded ahead of the scan
+  if (q0 + kPartPer <= a.n && (reinterpret_cast<uintptr_t>(a.idx_in + q0) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(a.flags + q0) & 3) == 0) {
+    static_assert(kPartPer == 4, "one 16-byte load of entries, one 4-byte load of flags");
+    const int4 v = *reinterpret_cast<const int4*>(a.idx_in + q0);
+    const uint32_t f4 = *reinterpret_cast<const uint32_t*>(a.flags + q0);
+    iv[0] = v.x;
+    iv[1] = v.y;
+    iv[2] = v.z;
+    iv[3] = v.w;
 #pragma unroll
-  for (int k = 0; k < kPartPer; ++k) {
-    const int64_t q = q0 + k;
-    fl[k] = (q < a.n) ? a.flags[q] : 0;
-    cnt += fl[k];
+    for (int k = 0; k < kPartPer; ++k) fl[k] = (uint8_t)((f4 >> (8 * k)) & 0xFFu);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPartPer; ++k) {
+      const int64_t q = q0 + k;
+      fl[k] = (q < a.n) ? a.flags[q] : 0;
+      iv[k] = (q < a.n) ? a.idx_in[q] : 0;
+    }
   }
+#pragma unroll
+  for (int k = 0; k < kPartPer; ++k) cnt += fl[k];
   // exclusive block scan of per-thread counts
   __shared__ int s_w[kPartThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -946,7 +1027,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(PartArgs a) {
         atomicOr(a.err, 1);
       } else if (nd.dst_one >= 0) {
         const int64_t dst = nd.dst_one + r1;
-        if (dst < a.n_out) a.idx_out[dst] = a.idx_in[q];
+        if (dst < a.n_out) a.idx_out[dst] = iv[k];
         else atomicOr(a.err, 8);
       }
     } else {
@@ -954,7 +1035,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(PartArgs a) {
         atomicOr(a.err, 2);
       } else if (nd.dst_zero >= 0) {
         const int64_t dst = nd.dst_zero + r0;
-        if (dst < a.n_out) a.idx_out[dst] = a.idx_in[q];
+        if (dst < a.n_out) a.idx_out[dst] = iv[k];
         else atomicOr(a.err, 8);
       }
     }
