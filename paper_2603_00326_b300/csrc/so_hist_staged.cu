@@ -38,6 +38,7 @@ constexpr int kStUMax = kTileF / 64;     // rows of a tile at St = 64 -> 128
 constexpr int kMmUMax = kTileF / 68;     // 120: every min/max group also fits the padded row-major tile
 constexpr int kStMaxWords = 2048;        // feature bitmap words (d <= 65536)
 constexpr int kMmPPW = 8;                // min/max: projections per warp
+constexpr int kMmBuf = 3;                // min/max: tile buffers (kMmBuf - 1 tiles in flight)
 constexpr int kMmGroup = kStWarps * kMmPPW;  // 256 projections per min/max group
 constexpr int kHistPGMax = 64;           // histogram projections per item (two per warp)
 constexpr int kHistPPW = kHistPGMax / kStWarps;  // histogram projections per warp
@@ -57,6 +58,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ---- shared-memory accesses by 32-bit shared address --------------------------
 // The inner loops address shared memory with 32-bit offsets in the shared
@@ -784,17 +787,19 @@ __device__ __forceinline__ void tile_labels(unsigned lab, int lane, int (&yo)[V 
 }
 
 // The item's tile loop, one instantiation per tile width St = 32 * V * NQ
-// (the same for every warp of the CTA).  Three tile buffers: tile tt+2 is
-// copied while tile tt is evaluated, one barrier per tile.  Warp w evaluates
-// its assigned projections, keeping each lane's running minima and maxima in
-// registers, and leaves them in s_pmin / s_pmax (only this warp touches its
-// rows).
+// (the same for every warp of the CTA).  kMmBuf tile buffers: tiles tt+1 ..
+// tt+kMmBuf-1 are in flight while tile tt is evaluated, one barrier per tile
+// (four and five buffers measured no faster than three, on contiguous and on
+// gathered items).  Warp w evaluates its assigned projections, keeping each
+// lane's running minima and maxima in registers, then reduces them over its
+// lanes into the node's keys (no shared-memory staging of the minima: the
+// 64 KB it took left the L1 cache less room, 0.680 -> 0.646 ms at the root).
 template <int V, int NQ, int KMAX>
 __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __restrict__ idx, const ItemPos& it,
                                         int U, bool contig, bool rowmaj, int Sp, float* s_tile, const int* s_rowfeat,
                                         const int64_t* s_rowoff, const int* s_assign, int nslot, const int* s_dk,
-                                        const uint32_t* s_dpk, float* s_pmin, float* s_pmax, int lane,
-                                        int warp, float* vbuf, int64_t n_total) {
+                                        const uint32_t* s_dpk, uint32_t* mm, int P, int lane, int warp, float* vbuf,
+                                        int64_t n_total) {
   constexpr int St = 32 * V * NQ;
   const int ntile = (int)((it.end - it.beg + St - 1) / St);
   const int* my = s_assign + warp * nslot;
@@ -811,19 +816,21 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
     pks[sl] = pl < 0 ? -1 : (pl | (s_dk[pl] << 16));
   }
   const Stager sg = stager_init(ds, idx, it, St, U, s_rowfeat, contig, rowmaj, Sp);
-  if (ntile > 0) stager_issue(sg, ds, idx, it, 0, St, U, s_rowoff, s_tile);
-  cp_async_commit();
-  if (ntile > 1) stager_issue(sg, ds, idx, it, 1, St, U, s_rowoff, s_tile + kTileF);
-  cp_async_commit();
-  int bc = 0, bi = 2;  // buffer of tile tt, buffer of tile tt + 2
+  // tiles 0 .. kMmBuf-2 in flight before the first is evaluated
+#pragma unroll
+  for (int b = 0; b < kMmBuf - 1; ++b) {
+    if (b < ntile) stager_issue(sg, ds, idx, it, b, St, U, s_rowoff, s_tile + b * kTileF);
+    cp_async_commit();
+  }
+  int bc = 0, bi = kMmBuf - 1;  // buffer of tile tt, buffer of tile tt + kMmBuf - 1
   for (int tt = 0; tt < ntile; ++tt) {
-    cp_async_wait1();
+    cp_async_wait_n<kMmBuf - 2>();
     __syncthreads();  // tile tt visible; every warp done with tile tt-1
-    if (tt + 2 < ntile) stager_issue(sg, ds, idx, it, tt + 2, St, U, s_rowoff, s_tile + bi * kTileF);
+    if (tt + kMmBuf - 1 < ntile) stager_issue(sg, ds, idx, it, tt + kMmBuf - 1, St, U, s_rowoff, s_tile + bi * kTileF);
     cp_async_commit();
     const unsigned tile = su32(s_tile) + 4u * kTileF * bc;
-    bc = bc == 2 ? 0 : bc + 1;
-    bi = bi == 2 ? 0 : bi + 1;
+    bc = bc == kMmBuf - 1 ? 0 : bc + 1;
+    bi = bi == kMmBuf - 1 ? 0 : bi + 1;
 #pragma unroll
     for (int sl = 0; sl < kMmPPW; ++sl) {
       if (pks[sl] < 0) break;
@@ -851,12 +858,17 @@ __device__ __forceinline__ void mm_item(const DatasetView& ds, const int32_t* __
       }
     }
   }
+  // the warp's projections: minimum and maximum over its lanes, into the
+  // node's order-preserving keys
 #pragma unroll
   for (int sl = 0; sl < kMmPPW; ++sl) {
     if (pks[sl] < 0) break;
     const int pl = pks[sl] & 0xffff;
-    s_pmin[pl * 32 + lane] = mns[sl];
-    s_pmax[pl * 32 + lane] = mxs[sl];
+    const float a = warp_min(mns[sl]), b = warp_max(mxs[sl]);
+    if (lane == 0) {
+      atomicMin(&mm[(it.h * P + it.p0 + pl) * 2], f2key(a));
+      atomicMax(&mm[(it.h * P + it.p0 + pl) * 2 + 1], f2key(b));
+    }
   }
 }
 
@@ -866,17 +878,15 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
                                                             int64_t n_total) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   const int nw = (ds.d + 31) >> 5;
-  float* s_tile = reinterpret_cast<float*>(s_raw);  // [3][kTileF]
-  float* s_pmin = s_tile + 3 * kTileF;                                     // [kMmGroup*32]
-  float* s_pmax = s_pmin + kMmGroup * 32;                                  // [kMmGroup*32]
-  uint32_t* s_dpk = reinterpret_cast<uint32_t*>(s_pmax + kMmGroup * 32);   // [kMmGroup*KMAX]
+  float* s_tile = reinterpret_cast<float*>(s_raw);  // [kMmBuf][kTileF]
+  uint32_t* s_dpk = reinterpret_cast<uint32_t*>(s_tile + kMmBuf * kTileF);  // [kMmGroup*KMAX]
   int* s_dk = reinterpret_cast<int*>(s_dpk + kMmGroup * KMAX);             // [kMmGroup]
   int* s_assign = s_dk + kMmGroup;                                         // [kMmGroup]
   int* s_rowfeat = s_assign + kMmGroup;                                    // [kStUMax]
   int64_t* s_rowoff = reinterpret_cast<int64_t*>(s_rowfeat + kStUMax);     // [kStUMax]
-  // the feature bitmap is only used while an item is set up, before tile 2
-  // is copied: it shares the third tile buffer
-  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_tile + 2 * kTileF);     // [nw]
+  // the feature bitmap is only used while an item is set up, before tile
+  // kMmBuf-1 is copied: it shares the last tile buffer
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_tile + (kMmBuf - 1) * kTileF);  // [nw]
   int* s_wpre = reinterpret_cast<int*>(s_bits + nw);                       // [nw]
   __shared__ int s_misc[kStWarps + 1];
   __shared__ int s_kcnt[kMaxCap + 1];
@@ -908,13 +918,13 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
     if (U <= kMmUMax) {
       if (St == 256)
         mm_item<4, 2, KMAX>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk,
-                            s_dpk, s_pmin, s_pmax, lane, warp, vbuf, n_total);
+                            s_dpk, mm, P, lane, warp, vbuf, n_total);
       else if (St == 128)
         mm_item<4, 1, KMAX>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk,
-                            s_dpk, s_pmin, s_pmax, lane, warp, vbuf, n_total);
+                            s_dpk, mm, P, lane, warp, vbuf, n_total);
       else
         mm_item<2, 1, KMAX>(ds, idx, it, U, contig, rowmaj, Sp, s_tile, s_rowfeat, s_rowoff, s_assign, nslot, s_dk,
-                            s_dpk, s_pmin, s_pmax, lane, warp, vbuf, n_total);
+                            s_dpk, mm, P, lane, warp, vbuf, n_total);
     } else {
       // direct path for wide groups: each warp gathers its projections' features
       for (int pl = warp; pl < it.np; pl += kStWarps) {
@@ -936,16 +946,12 @@ __global__ void __launch_bounds__(kStThreads, 1) k_mm_staged(DatasetView ds, con
           mx = fmaxf(mx, acc);
           if (vbuf) vbuf[(int64_t)(it.p0 + pl) * n_total + e] = acc;
         }
-        s_pmin[pl * 32 + lane] = mn;
-        s_pmax[pl * 32 + lane] = mx;
-      }
-    }
-    __syncthreads();
-    for (int pl = warp; pl < it.np; pl += kStWarps) {
-      const float a = warp_min(s_pmin[pl * 32 + lane]), b = warp_max(s_pmax[pl * 32 + lane]);
-      if (lane == 0) {
-        atomicMin(&mm[(it.h * P + it.p0 + pl) * 2], f2key(a));
-        atomicMax(&mm[(it.h * P + it.p0 + pl) * 2 + 1], f2key(b));
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0) {
+          atomicMin(&mm[(it.h * P + it.p0 + pl) * 2], f2key(mn));
+          atomicMax(&mm[(it.h * P + it.p0 + pl) * 2 + 1], f2key(mx));
+        }
       }
     }
   }
@@ -1448,8 +1454,7 @@ int hist_group_size(int B, int C, bool rw) {
 // buffer, so d does not change the size.
 static_assert(kStMaxWords * 8 <= kTileF * 4, "bitmap must fit a tile buffer");
 size_t mm_smem_bytes(int /*d*/, int kmax) {
-  return (size_t)3 * kTileF * 4 + (size_t)kMmGroup * 32 * 8 + (size_t)kMmGroup * kmax * 4 + kMmGroup * 8 +
-         kStUMax * 12;
+  return (size_t)kMmBuf * kTileF * 4 + (size_t)kMmGroup * kmax * 4 + kMmGroup * 8 + kStUMax * 12;
 }
 size_t hist_smem_bytes(int /*d*/, int kmax, int B, int C, int PG, bool rw) {
   const int npair = hist_pairs(PG);
