@@ -22,10 +22,12 @@ __device__ __forceinline__ V4 v4shfl_up(const V4& v, int o) {
             __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o)};
 }
 
-// Exclusive block scan of one V4 per thread; returns the exclusive prefix and
-// writes the block total into *total (all threads see it after return).
+// Exclusive block scan of one V4 per thread (NT threads); returns the
+// exclusive prefix and writes the block total into *total (all threads see it
+// after return).
+template <int NT = kScanThreads>
 __device__ __forceinline__ V4 block_excl_scan(V4 v, V4* total) {
-  __shared__ V4 warp_tot[kScanThreads / 32];
+  __shared__ V4 warp_tot[NT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   V4 inc = v;
 #pragma unroll
@@ -36,15 +38,15 @@ __device__ __forceinline__ V4 block_excl_scan(V4 v, V4* total) {
   if (lane == 31) warp_tot[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    V4 w = (lane < kScanThreads / 32) ? warp_tot[lane] : v4zero();
+    V4 w = (lane < NT / 32) ? warp_tot[lane] : v4zero();
     V4 wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const V4 u = v4shfl_up(wi, o);
       if (lane >= o) wi = v4add(wi, u);
     }
-    if (lane < kScanThreads / 32) warp_tot[lane] = V4{wi.x - w.x, wi.y - w.y, wi.z - w.z, wi.w - w.w};
-    if (lane == kScanThreads / 32 - 1) *total = wi;
+    if (lane < NT / 32) warp_tot[lane] = V4{wi.x - w.x, wi.y - w.y, wi.z - w.z, wi.w - w.w};
+    if (lane == NT / 32 - 1) *total = wi;
   }
   __syncthreads();
   const V4 wp = warp_tot[warp];
@@ -104,11 +106,32 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(F f, int64_t n, con
   }
 }
 
+// Small scans in one launch: one block of kScanSingleThreads threads, one
+// element per thread (a tree level's three launches of the general form cost
+// more than that).
+constexpr int kScanSingleThreads = 1024;
+constexpr int64_t kScanSingleMax = kScanSingleThreads;
+
+template <class F>
+__global__ void __launch_bounds__(kScanSingleThreads) k_scan_single(F f, int64_t n, V4* total) {
+  __shared__ V4 tot;
+  const int64_t i = threadIdx.x;
+  const V4 v = (i < n) ? f.value(i) : v4zero();
+  const V4 ex = block_excl_scan<kScanSingleThreads>(v, &tot);
+  if (i < n) f.apply(i, ex);
+  if (threadIdx.x == 0 && total) *total = tot;
+}
+
 // Runs the scan over n elements (n known on the host).  `tiles` needs
 // ceil(n / kScanTile) entries; the grand total goes to *total (device).
 template <class F>
 cudaError_t run_scan(const F& f, int64_t n, V4* tiles, V4* total, cudaStream_t st,
                      const char* name = "scan") {
+  if (n <= kScanSingleMax) {
+    ProfScope ps_(name, st, 1);
+    k_scan_single<F><<<1, kScanSingleThreads, 0, st>>>(f, n, total);
+    return cudaGetLastError();
+  }
   const int64_t n_tiles = (n + kScanTile - 1) / kScanTile;
   ProfScope ps_(name, st, n_tiles > 0 ? 3 : 1);
   if (n_tiles > 0) {
