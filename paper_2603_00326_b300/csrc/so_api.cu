@@ -751,6 +751,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
           a.bin_rule = tp->bin_rule;
           a.bin_keys = cur.key + j0;  // random-width boundaries from the node keys
           a.criterion = tp->criterion;
+          a.rows_trusted = 1;  // sampled by k_sample this level
           // most histogram-path nodes of a tree are gathered nodes of a few
           // thousand samples: smaller items balance the SMs better
           apply_tuning(a, tp->proj_per_cta, tp->chunk > 0 ? tp->chunk : 4096);

@@ -114,6 +114,9 @@ struct SearchArgs {
   // histogram-path sample's projected values and the histogram pass reads
   // them back instead of gathering the feature columns again
   float* vbuf = nullptr;
+  // projection rows sampled by this library (k_sample: distinct ascending
+  // features in [0, d), 1 <= length <= max_nnz), so they need no validation
+  int32_t rows_trusted = 0;
 };
 
 // Scratch of the staged-tile histogram kernels (so_hist_staged.cu).

@@ -600,7 +600,7 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
   // validation of the projection rows
   e = cudaMemsetAsync(s.err, 0, sizeof(int32_t) * ((size_t)a.m + 1), st);
   if (e != cudaSuccess) return e;
-  {
+  if (!a.rows_trusted) {
     const int64_t rows = (int64_t)a.m * P;
     if (rows > 0) k_validate_rows<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a.pv, a.m, a.ds.d, a.max_nnz, s.err);
   }
@@ -1367,25 +1367,24 @@ struct LevelF {
   }
 };
 
-__global__ void k_level_finish(const V4* total, Frontier nxt, LevelStats* stats) {
-  const V4 tt = *total;
-  nxt.off[tt.y] = tt.z;
-  stats->m_next = tt.y;
-  stats->n_next = tt.z;
-  stats->new_nodes = 2 * tt.x;
-}
+// The next frontier's end offset and the level's counts, from the level
+// scan's total (run by the scan's last step).
+struct LevelFinish {
+  Frontier nxt;
+  LevelStats* stats;
+  __device__ void operator()(const V4& tt) const {
+    nxt.off[tt.y] = tt.z;
+    stats->m_next = tt.y;
+    stats->n_next = tt.z;
+    stats->new_nodes = 2 * tt.x;
+  }
+};
 
 cudaError_t launch_tree_level(int32_t m, const Frontier cur, Frontier nxt, const so_split* splits,
                               const int64_t* left_counts, int32_t max_depth, int64_t node_base_next, TreeDev t,
                               PartNode* pnodes, V4* tiles, V4* total, LevelStats* stats, cudaStream_t st) {
   LevelF f{cur, nxt, splits, left_counts, max_depth, node_base_next, t, pnodes};
-  cudaError_t e = run_scan(f, m, tiles, total, st, "level_scan");
-  if (e != cudaSuccess) return e;
-  {
-    ProfScope ps_("k_level_finish", st);
-    k_level_finish<<<1, 1, 0, st>>>(total, nxt, stats);
-  }
-  return cudaGetLastError();
+  return run_scan(f, m, tiles, total, st, "level_scan", LevelFinish{nxt, stats});
 }
 
 }  // namespace sof

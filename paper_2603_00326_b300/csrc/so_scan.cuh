@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, int64_t n, V4
 }
 
 // One block: exclusive scan of the tile sums in place; total to *total.
-static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(V4* tiles, int64_t n_tiles, V4* total) {
+template <class Fin>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(V4* tiles, int64_t n_tiles, V4* total, Fin fin) {
   __shared__ V4 tot;
   V4 carry = v4zero();
   for (int64_t base = 0; base < n_tiles; base += kScanThreads) {
@@ -82,7 +83,10 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(V4* tiles, i
     carry = v4add(carry, tot);
     __syncthreads();
   }
-  if (threadIdx.x == 0 && total) *total = carry;
+  if (threadIdx.x == 0) {
+    if (total) *total = carry;
+    fin(carry);
+  }
 }
 
 template <class F>
@@ -112,24 +116,34 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(F f, int64_t n, con
 constexpr int kScanSingleThreads = 1024;
 constexpr int64_t kScanSingleMax = kScanSingleThreads;
 
-template <class F>
-__global__ void __launch_bounds__(kScanSingleThreads) k_scan_single(F f, int64_t n, V4* total) {
+// A scan's optional last step, given the grand total (after every apply).
+struct NoFinish {
+  __device__ void operator()(const V4&) const {}
+};
+
+template <class F, class Fin>
+__global__ void __launch_bounds__(kScanSingleThreads) k_scan_single(F f, int64_t n, V4* total, Fin fin) {
   __shared__ V4 tot;
   const int64_t i = threadIdx.x;
   const V4 v = (i < n) ? f.value(i) : v4zero();
   const V4 ex = block_excl_scan<kScanSingleThreads>(v, &tot);
   if (i < n) f.apply(i, ex);
-  if (threadIdx.x == 0 && total) *total = tot;
+  if (threadIdx.x == 0) {
+    if (total) *total = tot;
+    fin(tot);
+  }
 }
 
 // Runs the scan over n elements (n known on the host).  `tiles` needs
 // ceil(n / kScanTile) entries; the grand total goes to *total (device).
-template <class F>
+// fin(total) runs once the total is known; in the three-launch form that is
+// before the apply launch, so fin must not read what apply writes.
+template <class F, class Fin = NoFinish>
 cudaError_t run_scan(const F& f, int64_t n, V4* tiles, V4* total, cudaStream_t st,
-                     const char* name = "scan") {
+                     const char* name = "scan", Fin fin = Fin()) {
   if (n <= kScanSingleMax) {
     ProfScope ps_(name, st, 1);
-    k_scan_single<F><<<1, kScanSingleThreads, 0, st>>>(f, n, total);
+    k_scan_single<F, Fin><<<1, kScanSingleThreads, 0, st>>>(f, n, total, fin);
     return cudaGetLastError();
   }
   const int64_t n_tiles = (n + kScanTile - 1) / kScanTile;
@@ -137,7 +151,7 @@ cudaError_t run_scan(const F& f, int64_t n, V4* tiles, V4* total, cudaStream_t s
   if (n_tiles > 0) {
     k_scan_reduce<F><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(f, n, tiles);
   }
-  k_scan_tiles<<<1, kScanThreads, 0, st>>>(tiles, n_tiles, total);
+  k_scan_tiles<Fin><<<1, kScanThreads, 0, st>>>(tiles, n_tiles, total, fin);
   if (n_tiles > 0) {
     k_scan_apply<F><<<(unsigned)n_tiles, kScanThreads, 0, st>>>(f, n, tiles);
   }
