@@ -434,7 +434,7 @@ __device__ __forceinline__ int choose_st_pad(int U) {
 }
 
 // ---- k_groups: greedy projection groups per histogram node -------------------
-// One warp per node.  A group is closed before a projection that would push
+// One warp per (node, grouping).  A group is closed before a projection that would push
 // its distinct features above umax or its size above pmax.
 __global__ void __launch_bounds__(128) k_groups(const V4* plan_total, const int32_t* hist_nodes, ProjView pv, int d,
                                                 int umax1, int pmax1, int umax2, int pmax2, int32_t* ng1,
@@ -453,9 +453,12 @@ __global__ void __launch_bounds__(128) k_groups(const V4* plan_total, const int3
   const int P = pv.P;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t h = gw; h < m_hist; h += nwarps) {
+  // one warp per (node, pass): a node's two groupings run side by side
+  for (int64_t t = gw; t < 2 * m_hist; t += nwarps) {
+    const int64_t h = t >> 1;
+    const int pass = (int)(t & 1);
     const int64_t j = hist_nodes[h];
-    for (int pass = 0; pass < 2; ++pass) {
+    {
       const int umax = pass == 0 ? umax1 : umax2;
       const int pmax = pass == 0 ? pmax1 : pmax2;
       int32_t* gs = (pass == 0 ? gs1 : gs2) + h * (int64_t)(P + 1);
