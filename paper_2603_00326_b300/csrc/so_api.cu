@@ -698,6 +698,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
     if (hs.err & 16) return fail(SO_EINVAL, "root_idx holds a sample index outside [0, n)");
     if (hs.err & 32) return fail(SO_EINVAL, "a label is outside [0, n_classes)");
     int64_t m = hs.m_next, n_level = n_root, n_nodes = 1;
+    int64_t max_nv = hs.max_next;  // the current frontier's largest node
     Frontier cur = fa, nxt = fb;
     int32_t *cidx = idx_a, *nidx = idx_b;
     const float eps = effective_eps(tp->rescore_rel_eps, C);
@@ -752,6 +753,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
           a.bin_keys = cur.key + j0;  // random-width boundaries from the node keys
           a.criterion = tp->criterion;
           a.rows_trusted = 1;  // sampled by k_sample this level
+          a.max_nv_hint = max_nv;
           // most histogram-path nodes of a tree are gathered nodes of a few
           // thousand samples: smaller items balance the SMs better
           apply_tuning(a, tp->proj_per_cta, tp->chunk > 0 ? tp->chunk : 4096);
@@ -814,6 +816,7 @@ so_status so_train_tree(const so_dataset* ds, const int32_t* root_idx, int64_t n
       if (n_nodes > Ncap) return fail(SO_EINTERNAL, "node capacity exceeded");
       m = hs.m_next;
       n_level = hs.n_next;
+      max_nv = hs.max_next;
       std::swap(cur, nxt);
       std::swap(cidx, nidx);
     }

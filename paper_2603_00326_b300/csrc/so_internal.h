@@ -117,6 +117,9 @@ struct SearchArgs {
   // projection rows sampled by this library (k_sample: distinct ascending
   // features in [0, d), 1 <= length <= max_nnz), so they need no validation
   int32_t rows_trusted = 0;
+  // an upper bound of the nodes' sizes, or -1: below T no node takes the
+  // histogram path, so its launches are left out
+  int64_t max_nv_hint = -1;
 };
 
 // Scratch of the staged-tile histogram kernels (so_hist_staged.cu).
@@ -292,7 +295,7 @@ struct LevelStats {  // device-resident, read by the host once per level
   long long n_next;
   long long new_nodes;
   int err;
-  int pad;
+  int max_next;  // samples of the next frontier's largest node
 };
 
 cudaError_t launch_tree_root(const DatasetView ds, const int32_t* root_idx, int64_t n_root,

@@ -739,47 +739,51 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
     ProfScope ps_("k_xlnx_table", st);
     k_xlnx_table<<<kXlnxTab / 256, 256, 0, st>>>(s.xlnx);
   }
-  {
-    ProfScope ps_("k_hist_init", st);
-    k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
-  }
+  // the histogram path (no node of the call reaches T: left out)
+  const bool hist_any = a.hist_only || a.max_nv_hint < 0 || a.max_nv_hint >= a.T;
   const bool rw = a.bin_rule == SO_BINS_RANDOM_WIDTH;
-  if (staged_supported(a.ds.d)) {
-    e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, s.rw, S,
-                      a.max_nnz, st);
-    if (e != cudaSuccess) return e;
-  } else {
+  if (hist_any) {
     {
-      static thread_local int occ_mm = 0;
-      if (!occ_mm) occ_mm = occupancy(k_minmax<PG>, PG * 32, 0);
-      ProfScope ps_("k_minmax", st);
-      k_minmax<PG><<<di.num_sms * occ_mm, PG * 32, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
-                                                            s.hist_nodes, s.item_off, S, s.mm_keys);
+      ProfScope ps_("k_hist_init", st);
+      k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
     }
-    if (rw) {
-      e = launch_rw_bounds(a, s.plan_total, s.hist_nodes, s.mm_keys, s.rw, st);
+    if (staged_supported(a.ds.d)) {
+      e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, s.rw, S,
+                        a.max_nnz, st);
       if (e != cudaSuccess) return e;
+    } else {
+      {
+        static thread_local int occ_mm = 0;
+        if (!occ_mm) occ_mm = occupancy(k_minmax<PG>, PG * 32, 0);
+        ProfScope ps_("k_minmax", st);
+        k_minmax<PG><<<di.num_sms * occ_mm, PG * 32, 0, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
+                                                              s.hist_nodes, s.item_off, S, s.mm_keys);
+      }
+      if (rw) {
+        e = launch_rw_bounds(a, s.plan_total, s.hist_nodes, s.mm_keys, s.rw, st);
+        if (e != cudaSuccess) return e;
+      }
+      {
+        const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
+        e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int occ = occupancy(k_hist<PG>, PG * 32, smem);
+        ProfScope ps_("k_hist", st);
+        k_hist<PG><<<di.num_sms * occ, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
+                                                            s.hist_nodes, s.item_off, S, B, s.mm_keys, s.hist,
+                                                            rw ? s.rw.t : nullptr);
+      }
     }
     {
-      const size_t smem = (size_t)PG * B * C * sizeof(int32_t);
-      e = cudaFuncSetAttribute(k_hist<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      const int occ = occupancy(k_hist<PG>, PG * 32, smem);
-      ProfScope ps_("k_hist", st);
-      k_hist<PG><<<di.num_sms * occ, PG * 32, smem, st>>>(a.ds, a.idx, a.node_off, a.pv, s.plan_total,
-                                                          s.hist_nodes, s.item_off, S, B, s.mm_keys, s.hist,
-                                                          rw ? s.rw.t : nullptr);
+      ProfScope ps_("k_gini_scan", st);
+      k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, nullptr, cr);
     }
-  }
-  {
-    ProfScope ps_("k_gini_scan", st);
-    k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, nullptr, cr);
-  }
-  {
-    ProfScope ps_("k_hist_select", st);
-    k_hist_select<<<grid_fill, 256, 0, st>>>(s.plan_total, s.hist_nodes, a.node_off, P, B, C, s.hist, s.max32,
-                                             s.mm_keys, rw ? s.rw.t : nullptr, cr, a.out, a.left_counts);
-  }
+    {
+      ProfScope ps_("k_hist_select", st);
+      k_hist_select<<<grid_fill, 256, 0, st>>>(s.plan_total, s.hist_nodes, a.node_off, P, B, C, s.hist, s.max32,
+                                               s.mm_keys, rw ? s.rw.t : nullptr, cr, a.out, a.left_counts);
+    }
+  }  // hist_any
   // exact path (no node can take it when every node is on the histogram path
   // or T <= 2: nodes below 2 samples are never searched)
   if (!a.hist_only && a.T > 2) {
@@ -820,11 +824,11 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
   e = run_scan(pf, a.m, s.tiles, s.plan_total, st, "plan_scan");
   if (e != cudaSuccess) return e;
   const int grid_fill = di.num_sms * 8;
+  const bool rw = a.bin_rule == SO_BINS_RANDOM_WIDTH;
   {
     ProfScope ps_("k_hist_init", st);
     k_hist_init<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B * C, s.mm_keys, s.hist, s.max32);
   }
-  const bool rw = a.bin_rule == SO_BINS_RANDOM_WIDTH;
   if (staged_supported(a.ds.d)) {
     e = launch_staged(a, s.plan_total, s.hist_nodes, s.m_hist_cap, s.staged, s.mm_keys, s.hist, s.rw, S,
                       a.max_nnz, st);
@@ -1343,6 +1347,7 @@ __global__ void k_root_finish(int64_t n_root, uint64_t root_key, int32_t max_dep
   f.depth[0] = 0;
   stats->m_next = (active && stats->err == 0) ? 1 : 0;
   stats->n_next = n_root;
+  stats->max_next = (int)n_root;
   stats->new_nodes = 1;
 }
 
@@ -1404,6 +1409,7 @@ struct LevelF {
   int64_t node_base_next;
   TreeDev t;
   PartNode* pn;
+  LevelStats* stats;  // max_next: zeroed before the scan
 
   __device__ void children(int64_t j, bool& v, long long& nL, long long& nR, bool& aL, bool& aR, int* L,
                            int* R) const {
@@ -1449,6 +1455,11 @@ struct LevelF {
     nd.thr = v ? sp[j].threshold : 0.0f;
     nd.pad = 0;
     pn[j] = nd;
+    // the next frontier's largest node (an atomic only when this one is
+    // larger than the maximum seen so far)
+    const long long bl = aL ? nL : 0, br = aR ? nR : 0;
+    const int big = (int)(bl > br ? bl : br);
+    if (big > *(volatile int*)&stats->max_next) atomicMax(&stats->max_next, big);
     if (!v) return;
     const int64_t lid = node_base_next + 2 * ex.x;
     const int64_t rid = lid + 1;
@@ -1493,7 +1504,9 @@ struct LevelFinish {
 cudaError_t launch_tree_level(int32_t m, const Frontier cur, Frontier nxt, const so_split* splits,
                               const int64_t* left_counts, int32_t max_depth, int64_t node_base_next, TreeDev t,
                               PartNode* pnodes, V4* tiles, V4* total, LevelStats* stats, cudaStream_t st) {
-  LevelF f{cur, nxt, splits, left_counts, max_depth, node_base_next, t, pnodes};
+  LevelF f{cur, nxt, splits, left_counts, max_depth, node_base_next, t, pnodes, stats};
+  cudaError_t e = cudaMemsetAsync(&stats->max_next, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   return run_scan(f, m, tiles, total, st, "level_scan", LevelFinish{nxt, stats});
 }
 
