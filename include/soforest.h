@@ -377,10 +377,12 @@ so_status so_predict(const float *X, int64_t n, int32_t d, int64_t ld, const so_
  * projections per node with nnz = min(nnz_cap, d, 1+Poisson(lambda))), and
  * writes into params->sort_below the smallest measured size at which the
  * histogram path is no slower per node (2048 if it never is).  Then times the
- * histogram path of one node of min(n, 2^20) bootstrap-like samples for
- * proj_per_cta in {16, 32, 64} (those that fit) and chunk in {4096, 8192,
- * 16384} and writes the fastest pair into params->proj_per_cta and
- * params->chunk.  Other fields of params are kept.  Times per size go to times_ms_host [2*n_sizes] when
+ * histogram path for proj_per_cta in {16, 32, 64} (those that fit) and chunk
+ * in {4096, 8192, 16384} on two workloads -- one node of min(n, 2^20)
+ * bootstrap-like samples and a batch of up to 128 gathered nodes of 2048
+ * samples -- each the better of two timings, and writes into
+ * params->proj_per_cta and params->chunk the pair with the least sum of its
+ * times relative to each workload's fastest.  Other fields of params are kept.  Times per size go to times_ms_host [2*n_sizes] when
  * not NULL (exact, histogram), with the sizes in sizes_host [n_sizes];
  * n_sizes_out receives the count (at most 16).  The timed searches use
  * params->n_bins and params->bin_rule (random width with keys of their own;
