@@ -532,15 +532,23 @@ __global__ void __launch_bounds__(256) k_hist_select(const V4* plan_total, const
     }
     const float thr = key_thr(cr, M, n, C);
     Cand best{-1.0, INT_MAX, INT_MAX};
-    for (int p = warp; p < P; p += 8) {
-      if (max32[h * P + p] < thr) continue;
-      const int32_t* H = hist + (h * P + p) * (int64_t)B * C;
-      if (B <= 256 && C <= 2)
-        select_proj_regs<2>(H, B, C, lane, cr, thr, p, best);
-      else if (B <= 256 && C <= 4)
-        select_proj_regs<4>(H, B, C, lane, cr, thr, p, best);
-      else
-        select_proj(H, B, C, lane, cr, thr, p, best);
+    // warp w reads the float maxima of projections 256 i + w + 8 lane at
+    // once and walks those within the window (the lexicographic best does
+    // not depend on the order)
+    for (int base = 0; base < P; base += 8 * 32) {
+      const int pp = base + warp + 8 * lane;
+      unsigned hits = __ballot_sync(0xffffffffu, pp < P && max32[h * P + pp] >= thr);
+      while (hits) {
+        const int p = base + warp + 8 * (__ffs(hits) - 1);
+        hits &= hits - 1u;
+        const int32_t* H = hist + (h * P + p) * (int64_t)B * C;
+        if (B <= 256 && C <= 2)
+          select_proj_regs<2>(H, B, C, lane, cr, thr, p, best);
+        else if (B <= 256 && C <= 4)
+          select_proj_regs<4>(H, B, C, lane, cr, thr, p, best);
+        else
+          select_proj(H, B, C, lane, cr, thr, p, best);
+      }
     }
     best = warp_best(best);
     if (lane == 0) s_best[warp] = best;
