@@ -153,7 +153,7 @@ def profile_summary(name):
         return None
 
 
-def roofline_block(achieved, hbm, peak_kind, alg_bytes, k_avg_ms, clk):
+def roofline_block(achieved, hbm, peak_kind, alg_bytes, k_avg_ms, clk, full_size=True):
     """The histogram kernel against the measured HBM copy bandwidth, with its
     DRAM traffic and its two on-chip ceilings from the committed ncu summary
     of the same kernel source: the shared-memory pipe (one 128-byte wavefront
@@ -163,9 +163,10 @@ def roofline_block(achieved, hbm, peak_kind, alg_bytes, k_avg_ms, clk):
     out = {"bound": "hbm", "kernel": "k_hist", "achieved": achieved, "peak": hbm, "unit": "GB/s",
            "frac": (achieved / hbm) if achieved else None, "traffic": None, "peak_source": peak_kind,
            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": k_avg_ms}
-    rec = profile_summary("k_hist_staged_root_4m")
+    rec = profile_summary("k_hist_staged_root_4m") if full_size else None
     if rec is None or not k_avg_ms:
-        out["traffic_note"] = "no ncu summary of this kernel source under profiles/"
+        out["traffic_note"] = ("no ncu summary of this kernel source under profiles/" if full_size else
+                               "the committed ncu summary describes the full-size node, not this one")
         return out
     out["traffic"] = rec["dram_bytes_per_launch"]
     mhz = (clk or {}).get("sm_mhz") or 2032.0
@@ -752,7 +753,7 @@ def run_ours(args):
                 "pipelined": "step i+1's host-to-device copies overlap step i's kernels (two device input sets)",
                 "serial_value": (world * n * P / e2e_serial_s) if e2e_steps else None},
         "gpu_launches": int(launches),
-        "roofline": roofline_block(achieved, hbm, peak_kind, alg_bytes, k_avg_ms, clk),
+        "roofline": roofline_block(achieved, hbm, peak_kind, alg_bytes, k_avg_ms, clk, full_size=args.root_n is None),
         "stage_ms_per_launch": stage_ms,
         "stage_timing": f"a second pass of the {args.steps} steps with per-kernel CUDA events on the launching "
                         f"stream ({ms_traced:.4f} ms per step with the events)",
