@@ -455,8 +455,12 @@ def so_predict(X, forest: DeviceForest, want_votes: bool = False, stream=None):
     return pred, votes
 
 
+# the tuner's procedure: cached choices of an older procedure are not reused
+AUTOTUNE_VERSION = 2
+
+
 def _autotune_key(ds, n_proj, lam, cap, params, gpu: str) -> str:
-    return (f"{gpu}|n={ds.X.shape[1]}|d={ds.X.shape[0]}|C={ds.n_classes}|P={n_proj}|lam={lam}|cap={cap}"
+    return (f"v{AUTOTUNE_VERSION}|{gpu}|n={ds.X.shape[1]}|d={ds.X.shape[0]}|C={ds.n_classes}|P={n_proj}|lam={lam}|cap={cap}"
             f"|B={params.n_bins}|rule={params.bin_rule}|crit={params.criterion}|rowmajor={int(ds.Xr is not None)}")
 
 
