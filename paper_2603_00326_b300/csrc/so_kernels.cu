@@ -401,6 +401,9 @@ __device__ __forceinline__ float gini_proj_regs(const int32_t* __restrict__ H, i
   return best;
 }
 
+// REGS: the register walk (B <= 256 and C <= 2; the host picks the
+// instantiation, so each keeps its own register allocation)
+template <int REGS>
 __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t P, int32_t B, int32_t C,
                                                    const int32_t* __restrict__ hist, float* max32,
                                                    int32_t* node_counts, float* gain32_out, Crit cr) {
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(256) k_gini_scan(const V4* plan_total, int32_t
     BinWalk w;
     float best = key_none(cr);
     float* gain_row = gain32_out ? gain32_out + wi * (B - 1) : nullptr;
-    if (B <= 256 && C <= 2) {
+    if (REGS) {
       // (measured: for three classes the register form was slower here,
       // 0.023 against 0.015 ms for one 256-projection node)
       best = gini_proj_regs<2>(H, B, C, lane, cr, gain_row, w);
@@ -784,7 +787,8 @@ cudaError_t launch_search(const SearchArgs& a, const SearchScratch& s, cudaStrea
     }
     {
       ProfScope ps_("k_gini_scan", st);
-      k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, nullptr, cr);
+      auto kg = (B <= 256 && C <= 2) ? k_gini_scan<1> : k_gini_scan<0>;
+      kg<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, nullptr, cr);
     }
     {
       ProfScope ps_("k_hist_select", st);
@@ -862,7 +866,8 @@ cudaError_t launch_hist_inspect(const SearchArgs& a, const SearchScratch& s, flo
   }
   {
     ProfScope ps_("k_gini_scan", st);
-    k_gini_scan<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, gain_tmp,
+    auto kg = (B <= 256 && C <= 2) ? k_gini_scan<1> : k_gini_scan<0>;
+    kg<<<grid_fill, 256, 0, st>>>(s.plan_total, P, B, C, s.hist, s.max32, s.node_counts, gain_tmp,
                                            Crit{0, a.eps, nullptr});
   }
   {
