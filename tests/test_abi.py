@@ -211,3 +211,24 @@ def test_noalloc_shares_the_argument_checks(L):
     st = L.so_split_search_noalloc(C.byref(_fake_dataset(n_classes=8)), C.c_void_p(0x6000), 4000, C.byref(big),
                                    C.byref(S.split_params(256, 0, True)), C.byref(out), None, None)
     assert st == S.SO_EINVAL and "static" in S.so_last_error()
+
+
+@pytest.mark.parametrize("kw,n_root,root,what", [
+    (dict(n_proj=0), 10, 0x7000, "n_proj"), (dict(n_proj=1025), 10, 0x7000, "n_proj"),
+    (dict(cap=0), 10, 0x7000, "nnz_cap"), (dict(cap=33), 10, 0x7000, "nnz_cap"),
+    (dict(lam=-1.0), 10, 0x7000, "lambda"), (dict(lam=float("nan")), 10, 0x7000, "lambda"),
+    (dict(lam=float("inf")), 10, 0x7000, "lambda"),
+    (dict(n_bins=1), 10, 0x7000, "n_bins"), (dict(sort_below=5000), 10, 0x7000, "sort_below"),
+    (dict(), 0, 0x7000, "n_root"), (dict(), 10, 0, "root_idx"),
+])
+def test_tree_argument_checks(L, kw, n_root, root, what):
+    """so_train_tree rejects its parameters on the host, before any launch."""
+    from paper_2603_00326_b300 import soforest as S
+    ds = _fake_dataset()
+    base = dict(n_proj=8, lam=1.5, cap=8)
+    base.update(kw)
+    tp = S.tree_params(base.pop("n_proj"), base.pop("lam"), base.pop("cap"), **base)
+    out = S.so_tree()
+    st = L.so_train_tree(C.byref(ds), C.c_void_p(root), n_root, C.byref(tp), C.byref(out), None)
+    assert st == S.SO_EINVAL
+    assert what in S.so_last_error()
