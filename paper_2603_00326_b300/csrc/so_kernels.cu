@@ -13,7 +13,9 @@
 //               gain of every boundary, the projection's best (Section 3 step 3)
 //   k_hist_select per node: double re-score of the float near-ties, the
 //               lexicographic best (the paper's second GPU kernel)
-//   (exact path for small nodes: so_sort_warp.cu)
+//   (features up to 65536: the staged-tile kernels of so_hist_staged.cu
+//   take the place of k_minmax and k_hist; exact path for small nodes:
+//   so_sort_warp.cu)
 // plus the device sampler (Appendix A), the stable partition, and the
 // breadth-first frontier bookkeeping of tree growth.
 #include <algorithm>
